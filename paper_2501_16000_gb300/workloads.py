@@ -1,0 +1,198 @@
+"""Seeded synthetic inputs shaped like the benchmarks of arXiv 2501.16000 Sec. IV.
+
+This module holds input generators only: lattice sizes, relaxation times,
+wave vectors, initial density/velocity fields, batch mixes and arrival traces.
+It holds none of the scheme's arithmetic (no equilibrium, no collision, no
+streaming), so both the CUDA path's tests and the CPU oracle's tests may use it.
+
+Initial conditions:
+  * rotated decaying shear wave (Sec. IV, Eq. 18 generalised to any integer
+    wave vector on a periodic lattice):
+      k = 2 pi (m / nx, n / ny),  u(x) = u0 sin(k . x) e_perp,
+      e_perp = (-k_y, k_x) / |k|,  rho = rho0, no mean flow;
+  * isothermal shock tube (Sec. IV): rho = rho_left for x < x_split,
+    rho_right otherwise, u = 0, periodic in both axes.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+THETA0 = 1.0 / 3.0
+
+
+def shear_wave_phase(nx: int, ny: int, m: int, n: int) -> np.ndarray:
+    """k . x / (2 pi) reduced exactly to [0, 1) as a float64 array (ny, nx).
+
+    The integer numerator (m x ny + n y nx) mod (nx ny) is formed exactly, so
+    the phase carries a single rounding.
+    """
+    x = np.arange(nx, dtype=np.int64)[None, :]
+    y = np.arange(ny, dtype=np.int64)[:, None]
+    num = np.mod(m * x * ny + n * y * nx, nx * ny)
+    return num.astype(np.float64) / float(nx * ny)
+
+
+def shear_wave_direction(nx: int, ny: int, m: int, n: int) -> tuple[float, float]:
+    """Unit vector e_perp = (-k_y, k_x) / |k| for k = 2 pi (m / nx, n / ny)."""
+    kx, ky = m / nx, n / ny
+    norm = math.hypot(kx, ky)
+    if norm == 0.0:
+        raise ValueError("wave vector (m, n) must not be (0, 0)")
+    return -ky / norm, kx / norm
+
+
+def wave_number_sq(nx: int, ny: int, m: int, n: int) -> float:
+    """|k|^2 for k = 2 pi (m / nx, n / ny)."""
+    return (2.0 * math.pi) ** 2 * ((m / nx) ** 2 + (n / ny) ** 2)
+
+
+def shear_wave_fields(nx, ny, rho0, u0, m, n):
+    """(rho, ux, uy) float64 arrays (ny, nx) of the rotated shear wave."""
+    ph = shear_wave_phase(nx, ny, m, n)
+    s = np.sin(2.0 * np.pi * ph)
+    ex, ey = shear_wave_direction(nx, ny, m, n)
+    rho = np.full((ny, nx), float(rho0))
+    return rho, u0 * ex * s, u0 * ey * s
+
+
+def shock_tube_fields(nx, ny, rho_left, rho_right, x_split):
+    """(rho, ux, uy) of the isothermal shock tube, a density step at x_split."""
+    x = np.arange(nx)[None, :]
+    rho = np.where(x < x_split, float(rho_left), float(rho_right)) * np.ones((ny, 1))
+    z = np.zeros((ny, nx))
+    return rho, z, z.copy()
+
+
+def wave_vector_from_angle(nx: int, ny: int, phi: float, wavelength: float = 64.0):
+    """Integer (m, n) closest to a wave of the given wavelength at angle phi.
+
+    (m, n) = round(nx cos(phi) / lambda, ny sin(phi) / lambda); at least one is
+    nonzero.  Returns (m, n, realised angle in radians).
+    """
+    m = int(round(nx * math.cos(phi) / wavelength))
+    n = int(round(ny * math.sin(phi) / wavelength))
+    if m == 0 and n == 0:
+        if math.cos(phi) >= math.sin(phi):
+            m = 1
+        else:
+            n = 1
+    return m, n, math.atan2(n / ny, m / nx)
+
+
+# ---------------------------------------------------------------------------
+# Benchmark configurations (Sec. IV shapes; synthetic, seeded)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass(frozen=True)
+class LatticeCase:
+    """One lattice problem: geometry, physics and initial condition."""
+    nx: int
+    ny: int
+    tau: float
+    theta: float = THETA0
+    eq: str = "guided"          # "guided" (Eq. 11) or "poly2" (Eq. 15)
+    coll: str = "oreg"          # "oreg" (Eq. 7) or "bgk" (Eq. 1)
+    case: str = "shear"         # "shear" or "shock"
+    rho0: float = 1.0
+    u0: float = 0.05
+    m: int = 1
+    n: int = 0
+    rho_left: float = 1.5
+    rho_right: float = 0.75
+    x_split: int = 0
+    steps: int = 0
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny
+
+    def fields(self):
+        if self.case == "shear":
+            return shear_wave_fields(self.nx, self.ny, self.rho0, self.u0, self.m, self.n)
+        return shock_tube_fields(self.nx, self.ny, self.rho_left, self.rho_right, self.x_split)
+
+
+def shear_64(coll: str = "oreg", m: int = 2, n: int = 1) -> LatticeCase:
+    """64 x 64 periodic rotated shear wave, theta = 1/3, tau = 0.8, 1000 steps."""
+    return LatticeCase(nx=64, ny=64, tau=0.8, coll=coll, case="shear", u0=0.05,
+                       m=m, n=n, steps=1000)
+
+
+def shock_2048x4(eq: str = "guided", coll: str = "oreg") -> LatticeCase:
+    """2048 x 4 isothermal shock tube, 1.5 | 0.75 split at x = 1024, tau = 0.51."""
+    return LatticeCase(nx=2048, ny=4, tau=0.51, eq=eq, coll=coll, case="shock",
+                       rho_left=1.5, rho_right=0.75, x_split=1024, steps=2000)
+
+
+def large_shear(theta: float = THETA0, seed: int = 0, side: int = 8192,
+                steps: int = 500) -> LatticeCase:
+    """side x side rotated shear wave at a seeded random angle, tau = 0.6."""
+    rng = np.random.default_rng(seed)
+    phi = float(rng.uniform(0.0, math.pi / 2))
+    m, n, _ = wave_vector_from_angle(side, side, phi)
+    return LatticeCase(nx=side, ny=side, tau=0.6, theta=theta, case="shear",
+                       u0=0.05, m=m, n=n, steps=steps)
+
+
+def _log_uniform_int(rng, lo, hi):
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def batch_mix(count: int = 512, seed: int = 1, lo: int = 32, hi: int = 1024,
+              steps: int = 1000) -> list[LatticeCase]:
+    """Independent uneven lattices: sides log-uniform in [lo, hi] (non-square),
+    tau ~ U[0.51, 1.0], u0 ~ U[0.01, 0.1], angle ~ U[0, pi/2), case 50/50."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        nx = _log_uniform_int(rng, lo, hi)
+        ny = _log_uniform_int(rng, lo, hi)
+        tau = float(rng.uniform(0.51, 1.0))
+        u0 = float(rng.uniform(0.01, 0.1))
+        phi = float(rng.uniform(0.0, math.pi / 2))
+        shock = bool(rng.integers(0, 2))
+        if shock:
+            out.append(LatticeCase(nx=nx, ny=ny, tau=tau, case="shock",
+                                   x_split=nx // 2, steps=steps))
+        else:
+            m, n, _ = wave_vector_from_angle(nx, ny, phi)
+            out.append(LatticeCase(nx=nx, ny=ny, tau=tau, case="shear", u0=u0,
+                                   m=m, n=n, steps=steps))
+    return out
+
+
+@dataclasses.dataclass(frozen=True)
+class Request:
+    """One solve request of the serving trace."""
+    rid: int
+    arrival_s: float
+    lattice: LatticeCase
+
+
+def arrival_trace(count: int, rate_per_s: float, seed: int = 2, lo: int = 64,
+                  hi: int = 2048, steps_lo: int = 100, steps_hi: int = 10000
+                  ) -> list[Request]:
+    """Poisson arrivals of square shear/shock solves, sides log-uniform in
+    [lo, hi], step counts log-uniform in [steps_lo, steps_hi]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(count):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        side = _log_uniform_int(rng, lo, hi)
+        steps = _log_uniform_int(rng, steps_lo, steps_hi)
+        tau = float(rng.uniform(0.51, 1.0))
+        u0 = float(rng.uniform(0.01, 0.1))
+        phi = float(rng.uniform(0.0, math.pi / 2))
+        if bool(rng.integers(0, 2)):
+            lat = LatticeCase(nx=side, ny=side, tau=tau, case="shock",
+                              x_split=side // 2, steps=steps)
+        else:
+            m, n, _ = wave_vector_from_angle(side, side, phi)
+            lat = LatticeCase(nx=side, ny=side, tau=tau, case="shear", u0=u0,
+                              m=m, n=n, steps=steps)
+        out.append(Request(rid, t, lat))
+    return out
