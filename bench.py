@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the OReg D2Q9 stream-collide path on GB300.
+
+Default workload: one 8192 x 8192 periodic rotated shear wave (angle from
+seed 0, theta = 1/3, tau = 0.6, u0 = 0.05), guided equilibrium, OReg
+collision, FP32 storage and compute, A-B layout.  One "step" is one lattice
+time step (gather, moments, equilibrium, OReg projection, relaxation, store);
+the FP64 diagnostics reduction (mass, momentum, non-finite count) runs every
+100 steps inside the timed region.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (bounded sample of the same workload).
+
+Multi-GPU (torchrun, one rank per GPU): every rank advances its own
+independent lattice (weak scaling, no data-path collective); the timing is
+the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+DIAG_EVERY = 100
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--side", type=int, default=8192)
+    ap.add_argument("--theta", type=float, default=1.0 / 3.0)
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--layout", default="ab", choices=["ab", "aa"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-side", type=int, default=1024)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2501_16000_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel_key]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(args):
+    from paper_2501_16000_gb300 import workloads as W
+    return W.large_shear(theta=args.theta, seed=0, side=args.side, steps=args.steps)
+
+
+def cpu_baseline(args, case, seconds: float):
+    """The FP64 oracle, as it stands, on the host cores: the same lattice
+    parameters on a side x side periodic sample, stepped for ~seconds."""
+    from oracle import oracle as O
+    from paper_2501_16000_gb300 import workloads as W
+    side = args.cpu_sample_side
+    m, n, _ = W.wave_vector_from_angle(side, side, math.atan2(case.n / case.ny, case.m / case.nx))
+    p = O.params(side, side, case.tau, case.theta, O.GUIDED, O.OREG)
+    f = O.init_equilibrium(p, *W.shear_wave_fields(side, side, 1.0, case.u0, m, n))
+    threads = O.get_threads()
+    f = O.run(f, p, 1)  # warm-up
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        f = O.run(f, p, 2)
+        steps += 2
+    dt = time.perf_counter() - t0
+    mlups = side * side * steps / dt / 1e6
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{side}x{side} periodic shear wave, same tau/theta/u0, {steps} FP64 "
+                      f"steps in {dt:.1f} s, OpenMP over rows ({threads} threads)"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, rank 0 only."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2501_16000_gb300 import workloads as W
+    case = workload(args)
+    side = args.cpu_sample_side
+    m, n, _ = W.wave_vector_from_angle(side, side, math.atan2(case.n / case.ny, case.m / case.nx))
+    p = O.params(side, side, case.tau, case.theta, O.GUIDED, O.OREG)
+    f = O.init_equilibrium(p, *W.shear_wave_fields(side, side, 1.0, case.u0, m, n))
+    threads = O.get_threads()
+    # each benchmark step = one oracle lattice step on the sample; the sample
+    # shrinks if needed so that warm-up + steps stay within a few minutes
+    f = O.run(f, p, 1)
+    t0 = time.perf_counter()
+    f = O.run(f, p, 2)
+    per_step = (time.perf_counter() - t0) / 2
+    budget = 150.0
+    total = args.warmup + args.steps
+    while per_step * total > budget and side > 64:
+        side //= 2
+        per_step /= 4
+        m, n, _ = W.wave_vector_from_angle(side, side, math.atan2(case.n / case.ny, case.m / case.nx))
+        p = O.params(side, side, case.tau, case.theta, O.GUIDED, O.OREG)
+        f = O.init_equilibrium(p, *W.shear_wave_fields(side, side, 1.0, case.u0, m, n))
+    f = O.run(f, p, args.warmup)
+    t0 = time.perf_counter()
+    f = O.run(f, p, args.steps)
+    dt = time.perf_counter() - t0
+    mlups = side * side * args.steps / dt / 1e6
+    sample = (f"{side}x{side} periodic sample of the {case.nx}x{case.ny} shear wave "
+              f"(same tau/theta/u0), FP64 oracle, {threads} OpenMP threads")
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": round(mlups, 3), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"shear{case.nx}x{case.ny}-oreg-guided", "sample": sample},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2501_16000_gb300 import build
+    build.build()
+    from paper_2501_16000_gb300 import binding as B
+    from paper_2501_16000_gb300.engine import Lattice, bytes_per_node_step
+
+    case = workload(args)
+    N = case.nodes
+    stream = torch.cuda.Stream()
+    lat = Lattice(case.nx, case.ny, case.tau, case.theta, "guided", "oreg", args.storage,
+                  args.layout, stream=stream)
+    lat.init_case(case)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    with torch.cuda.stream(stream):
+        lat.step(args.warmup)
+        lat.diagnostics()
+    barrier()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for s in range(K):
+            ev[s][0].record(stream)
+            lat.step(1)
+            ev[s][1].record(stream)
+            launches += 1
+            if (s + 1) % DIAG_EVERY == 0:
+                d = lat.diagnostics()          # FP64 mass/momentum/non-finite check
+                launches += 2
+                if d["nonfinite"]:
+                    raise RuntimeError("non-finite populations")
+        t_end.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / K
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    mlups = world * N * K / (elapsed_ms / 1e3) / 1e6
+
+    bpn = bytes_per_node_step(args.storage)
+    peak, peak_kind = measured_peaks()
+    achieved = bpn * N / (kern_ms / 1e3) / 1e9
+    kernel_key = f"step_{args.layout}_{args.storage}_guided_oreg_{case.nx}x{case.ny}"
+    traffic = profiled_traffic(kernel_key)
+
+    # end to end through the public API: host fields (pinned) in, moments out
+    e2e = None
+    if not args.no_e2e:
+        h = [torch.empty((case.ny, case.nx), dtype=torch.float64, pin_memory=True)
+             for _ in range(6)]
+        rho, ux, uy = case.fields()
+        h[0].numpy()[:] = rho
+        h[1].numpy()[:] = ux
+        h[2].numpy()[:] = uy
+        barrier()
+        t0 = time.perf_counter()
+        lat.init_fields(h[0].numpy(), h[1].numpy(), h[2].numpy())
+        lat.step(K)
+        B.call("olb_moments", lat.handle, *[
+            a.numpy().ctypes.data_as(__import__("ctypes").POINTER(__import__("ctypes").c_double))
+            for a in h[3:6]], None)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": round(world * N * K / e2e_s / 1e6, 1), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(3 * N * 8 / K), "d2h_bytes_per_step": int(3 * N * 8 / K),
+               "note": f"one solve of {K} steps: olb_init_fields from pinned host fields, "
+                       f"olb_step, olb_moments to pinned host arrays"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, case, args.cpu_seconds)
+
+    lat.close()
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / K, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": f"shear{case.nx}x{case.ny}-oreg-guided-{args.layout}",
+                       "nodes": N, "theta": case.theta, "tau": case.tau, "u0": case.u0,
+                       "wave": [case.m, case.n], "storage": args.storage,
+                       "layout": args.layout, "diagnostics_every": DIAG_EVERY,
+                       "l2": f"inputs larger than L2 ({lat_bytes(args.storage, N) / 1e9:.1f} GB "
+                             f"state vs 126 MB L2)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "peak_kind": peak_kind,
+                         "bytes_per_node": bpn, "kernel_ms": round(kern_ms, 4)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def lat_bytes(storage, N):
+    from paper_2501_16000_gb300.engine import ELEM_BYTES
+    return 2 * 9 * N * ELEM_BYTES[storage]
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

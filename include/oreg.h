@@ -1,0 +1,192 @@
+/*
+ * oreg.h -- C ABI of the GB300 (sm_103a) Onsager-Regularized lattice
+ * Boltzmann library liboreg.so (D2Q9, arXiv 2501.16000).
+ *
+ * The library advances a periodic nx x ny D2Q9 lattice with the fused
+ * stream-and-collide update of the paper:
+ *
+ *   f_i(x + c_i, t + 1) = f_i^eq(x, t) + (1 - 1/tau) f_i^OReg(x, t)   (Eq. 7)
+ *
+ * where f^eq is the guided equilibrium (Eq. 11) or the second-order
+ * polynomial equilibrium (Eq. 15) and f^OReg is the local OReg projection of
+ * the non-equilibrium part f - f^eq (Eq. 6).  Lattice BGK (Eq. 1) is the
+ * switchable special case.  theta is a fixed per-lattice temperature
+ * (isothermal flow, Sec. II).
+ *
+ * Conventions shared by every call:
+ *   - Velocity order i = 0..8: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
+ *     (-1,-1) (1,-1).
+ *   - Host population arrays are double[9][ny][nx] (index (i*ny + y)*nx + x);
+ *     host field arrays are double[ny][nx] (index y*nx + x).
+ *   - The state of a lattice is always the canonical pre-collision
+ *     populations S_t at integer time t; storage precision, layout (A-B or
+ *     in-place AA) and parity are hidden behind the calls.
+ *   - Every call returns an olb_status and never aborts the process; on an
+ *     error the calling thread's message is available from olb_last_error().
+ *   - Calls that only enqueue device work are asynchronous on the lattice's
+ *     stream; calls that return data in host memory synchronise that stream.
+ *   - A lattice handle must not be used from two host threads at once.
+ */
+#ifndef OREG_H
+#define OREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct olb_lattice olb_lattice; /* opaque; owned by the library */
+
+typedef enum {
+    OLB_OK = 0,
+    OLB_ERR_INVALID = 1,   /* bad argument or parameter combination */
+    OLB_ERR_NOMEM = 2,     /* device or host allocation failed */
+    OLB_ERR_CUDA = 3,      /* a CUDA runtime call or launch failed */
+    OLB_ERR_NONFINITE = 4, /* the state holds NaN or Inf (outputs still written) */
+    OLB_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    OLB_ERR_STATE = 6      /* call not valid in the lattice's current state */
+} olb_status;
+
+typedef enum { OLB_EQ_GUIDED = 0, OLB_EQ_POLY2 = 1 } olb_equilibrium;
+typedef enum { OLB_COLL_OREG = 0, OLB_COLL_BGK = 1 } olb_collision;
+
+/* Population storage.  Every format stores shifted values g_i = f_i - s_i,
+ * with s_i the rest equilibrium w_i(theta) rho0 rounded to the compute type
+ * (w = (1-theta)^2, theta(1-theta)/2, theta^2/4 for rest, axis and diagonal
+ * directions).  F64 computes in double; F32, F16 and BF16 compute in float. */
+typedef enum {
+    OLB_F64 = 0,
+    OLB_F32 = 1,
+    OLB_F16_SHIFTED = 2,
+    OLB_BF16_SHIFTED = 3
+} olb_storage;
+
+/* A-B: two population buffers, pull streaming, buffers swap each step.
+ * AA: one buffer updated in place; even steps read and write a node's own
+ * slots (writing direction i into the opposite slot), odd steps read from
+ * and write to the neighbours.  Same results, half the memory. */
+typedef enum { OLB_LAYOUT_AB = 0, OLB_LAYOUT_AA = 1 } olb_layout;
+
+typedef struct {
+    int32_t nx, ny;        /* lattice size, >= 1 each; periodic in x and y */
+    double tau;            /* relaxation time, > 0.5 */
+    double theta;          /* guided: lattice temperature in (0, 1);
+                              poly2: must be 1/3 (theta0 of Eq. 15) */
+    double rho0;           /* reference density of the storage shift, > 0 (1 if unsure) */
+    int32_t eq;            /* olb_equilibrium */
+    int32_t coll;          /* olb_collision */
+    int32_t storage;       /* olb_storage */
+    int32_t layout;        /* olb_layout */
+    void *device_buffer;   /* optional caller-owned device memory for the
+                              populations (>= olb_required_bytes, 256-byte
+                              aligned); NULL: the library allocates.  Caller
+                              memory must outlive the lattice. */
+    size_t buffer_bytes;   /* size of device_buffer in bytes (ignored if NULL) */
+    void *cuda_stream;     /* cudaStream_t for all work of this lattice;
+                              NULL: the library creates and owns one */
+} olb_params;
+
+/* Tuning and precision options of a lattice (olb_set_option). */
+typedef enum {
+    /* 1: accumulate the conserved moments (mass, momentum) of the FP32
+       collision with error-free (TwoSum) additions, which keeps FP32 rounding
+       out of the conserved quantities; 0: plain sums.  Default 1 for
+       OLB_F32, ignored by the other formats. */
+    OLB_OPT_COMPENSATED = 1,
+    /* warps per thread block of the stream-collide kernels: 1, 2, 4 or 8
+       (default 8).  Each warp updates 32*V consecutive nodes of one row,
+       V = 16 bytes / element size. */
+    OLB_OPT_WARPS_PER_BLOCK = 2
+} olb_option;
+
+/* Version of this ABI (bumped on incompatible change). */
+int32_t olb_abi_version(void);
+
+/* Bytes of device memory the populations of a lattice with these
+ * parameters occupy (for admission control and caller allocation);
+ * 0 if the parameters are invalid.  Library scratch (a few MB at most) is
+ * extra and always library-owned. */
+size_t olb_required_bytes(const olb_params *p);
+
+/* Validates p, allocates the lattice and (unless p->device_buffer is
+ * given) its population memory.  The state is undefined until one of the
+ * olb_init_* or olb_set_populations calls.  *out receives the handle. */
+olb_status olb_create_lattice(const olb_params *p, olb_lattice **out);
+
+/* S_0 = f^eq(rho, u) of a rotated decaying shear wave (Sec. IV, Eq. 18 with
+ * any integer wave vector): k = 2 pi (m/nx, n/ny), u = u0 sin(k.x) e_perp,
+ * e_perp = (-k_y, k_x)/|k|, rho = rho0.  (m, n) != (0, 0).  Sets t = 0. */
+olb_status olb_init_shear_wave(olb_lattice *lat, double rho0, double u0, int32_t m,
+                               int32_t n);
+
+/* S_0 = f^eq of the isothermal shock tube (Sec. IV): rho = rho_left for
+ * x < x_split, rho_right otherwise, u = 0.  Sets t = 0. */
+olb_status olb_init_shock_tube(olb_lattice *lat, double rho_left, double rho_right,
+                               int32_t x_split);
+
+/* S_0 = f^eq(rho(x), u(x)) from host fields rho, ux, uy (double[ny][nx]).
+ * Copies host -> device inside the call; the arrays may be reused on return.
+ * Sets t = 0. */
+olb_status olb_init_fields(olb_lattice *lat, const double *rho, const double *ux,
+                           const double *uy);
+
+/* Advances nsteps >= 0 time steps (Eq. 7, or Eq. 1 for BGK) asynchronously
+ * on the lattice's stream. */
+olb_status olb_step(olb_lattice *lat, int64_t nsteps);
+
+/* Sets an olb_option; takes effect from the next olb_step. */
+olb_status olb_set_option(olb_lattice *lat, int32_t option, int64_t value);
+
+/* Current integer time t of the canonical state (-1 before any init). */
+int64_t olb_time(const olb_lattice *lat);
+
+/* Macroscopic fields of S_t into host arrays double[ny][nx]:
+ * rho = <f,1>, u = <f,c>/rho (Eq. 2a) and, if theta_loc != NULL, the local
+ * temperature (<f,c^2> - rho u^2)/(2 rho) (from E = (D p + rho u^2)/2,
+ * p = rho theta).  Synchronises the stream. */
+olb_status olb_moments(olb_lattice *lat, double *rho, double *ux, double *uy,
+                       double *theta_loc);
+
+/* Same fields written to caller device arrays (double[ny][nx], any may be
+ * NULL except rho), asynchronously on the lattice's stream. */
+olb_status olb_moments_device(olb_lattice *lat, double *d_rho, double *d_ux,
+                              double *d_uy, double *d_theta_loc);
+
+/* Canonical S_t into host double[9][ny][nx].  Synchronises the stream. */
+olb_status olb_get_populations(olb_lattice *lat, double *f9);
+
+/* Canonical S_t of the window [x0, x0 + wx) x [y0, y0 + wy) into host
+ * double[9][wy][wx] (sampled checks of lattices too large to copy whole).
+ * Synchronises the stream. */
+olb_status olb_get_region(olb_lattice *lat, int32_t x0, int32_t y0, int32_t wx, int32_t wy,
+                          double *f9);
+
+/* Replaces the state by host double[9][ny][nx] (canonical populations) at
+ * time t (>= 0); the arrays may be reused on return. */
+olb_status olb_set_populations(olb_lattice *lat, const double *f9, int64_t t);
+
+/* FP64 reductions of S_t: total mass sum rho, momentum sum rho u, and the
+ * number of nodes whose populations are not all finite.  Returns
+ * OLB_ERR_NONFINITE (after writing the outputs) if that number is > 0.
+ * Synchronises the stream. */
+olb_status olb_diagnostics(olb_lattice *lat, double *mass, double *mom_x, double *mom_y,
+                           int64_t *nonfinite);
+
+/* FP64 projection of the velocity of S_t on a shear-wave mode:
+ * A = (2 / (nx ny)) sum_x u(x) . e_perp sin(k . x), k = 2 pi (m/nx, n/ny);
+ * the decay statistic of Sec. IV.  Synchronises the stream. */
+olb_status olb_wave_amplitude(olb_lattice *lat, int32_t m, int32_t n, double *amp);
+
+/* Releases the lattice and everything it allocated (NULL is a no-op).
+ * Waits for the lattice's pending work first. */
+olb_status olb_destroy(olb_lattice *lat);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *olb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OREG_H */

@@ -1,0 +1,342 @@
+// Device-side building blocks of the OReg D2Q9 stream-collide path (sm_103a).
+//
+//   * D2Q9 velocity set and opposite-direction table (Fig. 1a).
+//   * Storage codecs: every format holds shifted populations g_i = f_i - s_i.
+//   * The per-node collision: moments (Eq. 2a), guided (Eq. 11) or polynomial
+//     (Eq. 15) equilibrium, the OReg projection (Eq. 6) and the update of
+//     Eq. 7, or lattice BGK (Eq. 1), all written in deviation variables so
+//     that no O(1) quantity is formed and then cancelled in low precision.
+//   * Warp-level shifted row-segment loads (pull streaming) and stores (push
+//     streaming of the in-place AA layout) on 16-byte vectors.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace oreg {
+
+// ---------------------------------------------------------------------------
+// D2Q9 velocity set, order (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx_of(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int i) {
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp_of(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+// Component index of a velocity component: 0 -> 0, +1 -> 1, -1 -> 2.
+__host__ __device__ constexpr int kidx(int c) { return c == 0 ? 0 : (c > 0 ? 1 : 2); }
+
+static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp");
+static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp");
+
+enum { EQ_GUIDED = 0, EQ_POLY2 = 1 };
+enum { COLL_OREG = 0, COLL_BGK = 1 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+// ---------------------------------------------------------------------------
+// Storage traits: T = stored element, C = compute type, V = elements per 16 B.
+// ---------------------------------------------------------------------------
+template <int S> struct Storage;
+template <> struct Storage<ST_F64> {
+    using T = double; using C = double; static constexpr int V = 2;
+    __device__ static C dec(T v) { return v; }
+    __device__ static T enc(C v) { return v; }
+};
+template <> struct Storage<ST_F32> {
+    using T = float; using C = float; static constexpr int V = 4;
+    __device__ static C dec(T v) { return v; }
+    __device__ static T enc(C v) { return v; }
+};
+template <> struct Storage<ST_F16> {
+    using T = __half; using C = float; static constexpr int V = 8;
+    __device__ static C dec(T v) { return __half2float(v); }
+    __device__ static T enc(C v) { return __float2half_rn(v); }
+};
+template <> struct Storage<ST_BF16> {
+    using T = __nv_bfloat16; using C = float; static constexpr int V = 8;
+    __device__ static C dec(T v) { return __bfloat162float(v); }
+    __device__ static T enc(C v) { return __float2bfloat16_rn(v); }
+};
+
+// 16-byte vector of V stored elements.
+template <int S> struct Vec {
+    using ST = Storage<S>;
+    union { uint4 raw; typename ST::T e[ST::V]; };
+};
+
+template <int S>
+__device__ __forceinline__ Vec<S> ld_vec(const typename Storage<S>::T *p) {
+    Vec<S> v;
+    v.raw = *reinterpret_cast<const uint4 *>(p);
+    return v;
+}
+template <int S>
+__device__ __forceinline__ Vec<S> ld_vec_nc(const typename Storage<S>::T *p) {
+    Vec<S> v;
+    v.raw = __ldg(reinterpret_cast<const uint4 *>(p));
+    return v;
+}
+template <int S>
+__device__ __forceinline__ void st_vec(typename Storage<S>::T *p, const Vec<S> &v) {
+    *reinterpret_cast<uint4 *>(p) = v.raw;
+}
+
+// ---------------------------------------------------------------------------
+// Per-lattice constants of the collision (computed in FP64 on the host).
+// ---------------------------------------------------------------------------
+template <typename C> struct CollConst {
+    C rho0;          // reference density of the shift
+    C psi0[3];       // 1-D rest factors: guided Psi_0(0) = 1 - theta, Psi_+-(0) = theta/2;
+                     // poly2 W_0 = 1 - theta0, W_+- = theta0 / 2
+    C w[9];          // W_i = psi0[a] psi0[b]
+    C shift[9];      // storage shift s_i (rest equilibrium rounded to C)
+    C corr[9];       // W_i rho0 - s_i (exact difference, rounded to C)
+    C sum_corr;      // sum_i corr_i
+    C lam;           // 1 - 1/tau
+    C inv_2th2;      // 1 / (2 theta^2), theta = lattice theta (guided) or theta0 (poly2)
+    C theta;         // lattice theta (guided) or theta0 (poly2)
+};
+
+// Error-free sum: a + b = s + e exactly (Knuth TwoSum).
+template <typename C>
+__device__ __forceinline__ void two_sum(C a, C b, C &s, C &e) {
+    s = a + b;
+    C bp = s - a;
+    C ap = s - bp;
+    e = (a - ap) + (b - bp);
+}
+
+// Conserved moments of one node from its shifted populations g.
+//   drho = rho - rho0 = sum g_i - sum corr_i,  j = sum c_i g_i
+// (the shifts cancel in j because opposite directions share one shift).
+// COMP selects compensated (TwoSum) accumulation.
+template <typename C, bool COMP>
+__device__ __forceinline__ void conserved(const C g[9], const CollConst<C> &k, C &drho,
+                                          C &jx, C &jy) {
+    if constexpr (!COMP) {
+        drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8]) -
+               k.sum_corr;
+        jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
+        jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
+    } else {
+        C s = g[0], e = C(0), t;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) { two_sum(s, g[i], s, t); e += t; }
+        drho = (s - k.sum_corr) + e;
+        C sx = g[1], ex = C(0);
+        two_sum(sx, -g[3], sx, t); ex += t;
+        two_sum(sx, g[5], sx, t); ex += t;
+        two_sum(sx, -g[6], sx, t); ex += t;
+        two_sum(sx, -g[7], sx, t); ex += t;
+        two_sum(sx, g[8], sx, t); ex += t;
+        jx = sx + ex;
+        C sy = g[2], ey = C(0);
+        two_sum(sy, -g[4], sy, t); ey += t;
+        two_sum(sy, g[5], sy, t); ey += t;
+        two_sum(sy, g[6], sy, t); ey += t;
+        two_sum(sy, -g[7], sy, t); ey += t;
+        two_sum(sy, -g[8], sy, t); ey += t;
+        jy = sy + ey;
+    }
+}
+
+// One node's collision in shifted variables: g (pre-collision, f - s) in,
+// post (post-collision, f - s) out.
+//
+// Moments: rho = rho0 + drho, u = j / rho; the trace-free non-equilibrium
+// stress of Eq. 6's inner sum, S_ab = sum_k (c_ka c_kb - c_k^2 delta_ab / 2)
+// f^neq_k, equals Pi - Pi^eq with Pi^eq = rho theta delta + rho u u for both
+// equilibria, so S_xx = ((Pi_xx - Pi_yy) - rho (u_x^2 - u_y^2)) / 2 and
+// S_xy = Pi_xy - rho u_x u_y (the shifts cancel in Pi_xx - Pi_yy and Pi_xy).
+// Equilibrium deviation geq_i = f^eq_i - s_i:
+//   guided (Eq. 11, f^eq = rho Psi_a(u_x) Psi_b(u_y)):
+//     geq = drho W + rho (dPsi_a Psi_b + Psi_a(0) dPsi_b) + corr, with
+//     dPsi_0 = -u^2, dPsi_+- = (+-u + u^2)/2;
+//   poly2 (Eq. 15): geq = W (drho + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u^2)) + corr.
+// OReg (Eqs. 6, 7): f^OReg_i = f^eq_i / (2 rho theta^2)
+//   [(C_x^2 - C_y^2) S_xx + 2 C_x C_y S_xy], C = c - u (the delta terms of
+// Eq. 6 vanish because S is trace-free), post = geq + (1 - 1/tau) f^OReg.
+// BGK (Eq. 1): post = geq + (1 - 1/tau) (g - geq).
+template <int EQ, int COLL, typename C, bool COMP>
+__device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst<C> &k) {
+    C drho, jx, jy;
+    conserved<C, COMP>(g, k, drho, jx, jy);
+    const C rho = k.rho0 + drho;
+    const C inv_rho = C(1) / rho;
+    const C ux = jx * inv_rho, uy = jy * inv_rho;
+    const C ux2 = ux * ux, uy2 = uy * uy;
+
+    C geq[9];
+    if constexpr (EQ == EQ_GUIDED) {
+        const C dpx[3] = {-ux2, C(0.5) * (ux + ux2), C(0.5) * (ux2 - ux)};
+        const C dpy[3] = {-uy2, C(0.5) * (uy + uy2), C(0.5) * (uy2 - uy)};
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
+            const C psib = k.psi0[b] + dpy[b];
+            geq[i] = fma(drho, k.w[i], fma(rho, fma(dpx[a], psib, k.psi0[a] * dpy[b]), k.corr[i]));
+        }
+    } else {
+        const C u2 = ux2 + uy2;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const C cu = C(cx_of(i)) * ux + C(cy_of(i)) * uy;
+            const C poly = fma(C(3), cu, fma(C(4.5) * cu, cu, C(-1.5) * u2));
+            geq[i] = fma(k.w[i], fma(rho, poly, drho), k.corr[i]);
+        }
+    }
+
+    if constexpr (COLL == COLL_BGK) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) post[i] = fma(k.lam, g[i] - geq[i], geq[i]);
+    } else {
+        const C dxy = (g[1] + g[3]) - (g[2] + g[4]);
+        const C pxy = (g[5] + g[7]) - (g[6] + g[8]);
+        const C sxx = C(0.5) * (dxy - rho * (ux2 - uy2));
+        const C sxy = pxy - rho * ux * uy;
+        const C a = k.lam * k.inv_2th2 * inv_rho;
+        const C X[3] = {-ux, C(1) - ux, C(-1) - ux};
+        const C Y[3] = {-uy, C(1) - uy, C(-1) - uy};
+        const C two_sxy = C(2) * sxy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ia = kidx(cx_of(i)), ib = kidx(cy_of(i));
+            const C d = fma(X[ia] * X[ia] - Y[ib] * Y[ib], sxx, X[ia] * Y[ib] * two_sxy);
+            const C feq = k.shift[i] + geq[i];
+            post[i] = fma(feq, a * d, geq[i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level shifted row-segment access.
+//
+// A warp owns 32*V consecutive nodes x = xb .. xb+V-1 per lane (xb = seg*32V +
+// lane*V) of one row; row storage has a pitch that is a multiple of V, so a
+// lane's V elements are one aligned 16-byte vector.  Lanes with xb >= nx are
+// idle but still take part in the shuffles.
+// ---------------------------------------------------------------------------
+
+// Pull: out[j] = value at x - CX (periodic in x) of node x = xb + j, read from
+// the row at rowp.  NC selects the read-only data path (A-B layout).
+template <int S, int CX, bool NC>
+__device__ __forceinline__ void load_row_shifted(const typename Storage<S>::T *rowp, int xb,
+                                                 int nx, int lane,
+                                                 typename Storage<S>::C out[Storage<S>::V]) {
+    using ST = Storage<S>;
+    using C = typename ST::C;
+    constexpr int V = ST::V;
+    const bool active = xb < nx;
+    C a[V];
+    if (active) {
+        Vec<S> v = NC ? ld_vec_nc<S>(rowp + xb) : ld_vec<S>(rowp + xb);
+#pragma unroll
+        for (int j = 0; j < V; ++j) a[j] = ST::dec(v.e[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) a[j] = C(0);
+    }
+    if constexpr (CX == 0) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) out[j] = a[j];
+    } else if constexpr (CX == 1) {
+        // left neighbour of the lane's first node
+        C left = __shfl_up_sync(0xffffffffu, a[V - 1], 1);
+        if (active && (lane == 0 || xb == 0)) left = ST::dec(rowp[xb == 0 ? nx - 1 : xb - 1]);
+        out[0] = left;
+#pragma unroll
+        for (int j = 1; j < V; ++j) out[j] = a[j - 1];
+    } else {
+        // right neighbour of the lane's last node; node nx-1 wraps to x = 0
+        C right = __shfl_down_sync(0xffffffffu, a[0], 1);
+        if (active && lane == 31 && xb + V < nx) right = ST::dec(rowp[xb + V]);
+        C wrapv = C(0);
+        if (active && xb + V >= nx) wrapv = ST::dec(rowp[0]);
+#pragma unroll
+        for (int j = 0; j < V - 1; ++j) out[j] = a[j + 1];
+        out[V - 1] = right;
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+            if (xb + j == nx - 1) out[j] = wrapv;
+    }
+}
+
+// Push: the value p[j] of node x = xb + j goes to position x + CX (periodic)
+// of the row at rowp.  Each position is written exactly once, by the lane
+// that owns the node the value comes from; positions past nx (row padding)
+// may receive garbage.
+template <int S, int CX>
+__device__ __forceinline__ void store_row_shifted(typename Storage<S>::T *rowp, int xb, int nx,
+                                                  int lane,
+                                                  const typename Storage<S>::C p[Storage<S>::V]) {
+    using ST = Storage<S>;
+    using C = typename ST::C;
+    constexpr int V = ST::V;
+    const bool active = xb < nx;
+    if constexpr (CX == 0) {
+        if (active) {
+            Vec<S> v;
+#pragma unroll
+            for (int j = 0; j < V; ++j) v.e[j] = ST::enc(p[j]);
+            st_vec<S>(rowp + xb, v);
+        }
+    } else if constexpr (CX == 1) {
+        // position xb + j receives node xb + j - 1
+        const C from_left = __shfl_up_sync(0xffffffffu, p[V - 1], 1);
+        if (active) {
+            Vec<S> v;
+            v.e[0] = ST::enc(from_left);
+#pragma unroll
+            for (int j = 1; j < V; ++j) v.e[j] = ST::enc(p[j - 1]);
+            const bool first_foreign = (lane == 0) || (xb == 0);
+            if (!first_foreign) {
+                st_vec<S>(rowp + xb, v);
+            } else {
+#pragma unroll
+                for (int j = 1; j < V; ++j) rowp[xb + j] = v.e[j];
+            }
+            // values whose target lies outside this lane's vector
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int x = xb + j;
+                if (x == nx - 1) rowp[0] = ST::enc(p[j]);
+            }
+            if (lane == 31 && xb + V < nx) rowp[xb + V] = ST::enc(p[V - 1]);
+        }
+    } else {
+        // position xb + j receives node xb + j + 1
+        const C from_right = __shfl_down_sync(0xffffffffu, p[0], 1);
+        if (active) {
+            Vec<S> v;
+#pragma unroll
+            for (int j = 0; j < V - 1; ++j) v.e[j] = ST::enc(p[j + 1]);
+            v.e[V - 1] = ST::enc(from_right);
+            const bool has_row_end = xb + V > nx - 1;           // holds position nx-1
+            const bool last_foreign = (lane == 31) && (xb + V < nx);
+            if (!has_row_end && !last_foreign) {
+                st_vec<S>(rowp + xb, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const int x = xb + j;
+                    const bool foreign = (x == nx - 1) || (j == V - 1 && last_foreign) || (x >= nx);
+                    if (!foreign) rowp[x] = v.e[j];
+                }
+            }
+            // node xb's value goes to position xb - 1 (wrapping at the row start)
+            if (xb == 0) rowp[nx - 1] = ST::enc(p[0]);
+            else if (lane == 0) rowp[xb - 1] = ST::enc(p[0]);
+        }
+    }
+}
+
+__device__ __forceinline__ int wrap_row(int y, int ny) {
+    return y < 0 ? y + ny : (y >= ny ? y - ny : y);
+}
+
+}  // namespace oreg

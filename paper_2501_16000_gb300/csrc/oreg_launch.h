@@ -1,0 +1,78 @@
+// Host-side launch interface between the C ABI (oreg_api.cu) and the kernels,
+// which are instantiated once per storage format (oreg_st_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace oreg {
+
+template <typename C> struct CollConst;
+
+// Geometry of a population state: planes of ny rows of `pitch` elements; the
+// first nx elements of a row are nodes, the rest padding.  aa_odd selects the
+// odd-step addressing of the in-place layout.
+struct StateGeom {
+    int nx, ny, pitch;
+    size_t plane;  // elements per population plane
+    int aa_odd;
+};
+
+struct StepArgs {
+    void *src;         // A-B: buffer of S_t; AA: the single buffer
+    void *dst;         // A-B: buffer of S_{t+1}; AA: unused
+    int nx, ny, pitch;
+    size_t plane;
+    int segs;          // row segments of 32*V nodes per row
+    int eq, coll, layout, parity;
+    int comp;          // compensated conserved-moment sums (FP32 only)
+    int warps_per_block;
+    const void *kconst;  // CollConst<C> of the storage's compute type
+    cudaStream_t stream;
+};
+
+enum { INIT_SHEAR = 0, INIT_SHOCK = 1, INIT_FIELDS = 2 };
+
+struct InitSpec {
+    int mode;
+    double rho_a, rho_b;  // shear: rho0; shock: left/right density
+    double u0, ex, ey;    // shear amplitude and direction e_perp
+    int m, n;             // shear wave vector integers
+    int x_split;          // shock split column
+    const double *rho, *ux, *uy;  // fields mode: device arrays [rows][nx]
+    int y0, rows;                 // rows initialised by this launch
+};
+
+struct ModeSpec {
+    int active;
+    int m, n;
+    double ex, ey;
+};
+
+#define OREG_DECLARE_LAUNCHERS(SUFFIX)                                                            \
+    cudaError_t step_##SUFFIX(const StepArgs &a);                                                 \
+    cudaError_t init_##SUFFIX(void *b, const StateGeom &g, const InitSpec &sp, int eq,            \
+                              const CollConst<double> &kd, cudaStream_t s);                       \
+    cudaError_t get_canonical_##SUFFIX(const void *b, const StateGeom &g, int x0, int y0, int wx, \
+                                       int wy, const CollConst<double> &kd, double *out,          \
+                                       cudaStream_t s);                                           \
+    cudaError_t set_canonical_##SUFFIX(void *b, const StateGeom &g, int y0, int rows,             \
+                                       const CollConst<double> &kd, const double *in,             \
+                                       cudaStream_t s);                                           \
+    cudaError_t moments_##SUFFIX(const void *b, const StateGeom &g, int y0, int rows,             \
+                                 const CollConst<double> &kd, double *r, double *ux, double *uy,  \
+                                 double *th, cudaStream_t s);                                     \
+    cudaError_t reduce_##SUFFIX(const void *b, const StateGeom &g, const CollConst<double> &kd,   \
+                                const ModeSpec &m, double *partials, int nblocks, double *out,    \
+                                cudaStream_t s);
+
+OREG_DECLARE_LAUNCHERS(f64)
+OREG_DECLARE_LAUNCHERS(f32)
+OREG_DECLARE_LAUNCHERS(f16)
+OREG_DECLARE_LAUNCHERS(bf16)
+
+constexpr int RED_BLOCKS_MAX = 1216;  // fixed reduction grid (8 x 152 SMs)
+constexpr int RED_QUANTITIES = 5;
+
+}  // namespace oreg

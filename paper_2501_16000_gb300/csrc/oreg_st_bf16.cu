@@ -1,0 +1,4 @@
+// Kernel instantiations for bf16 population storage.
+#include "oreg_kernels.cuh"
+
+OREG_DEFINE_LAUNCHERS(bf16, oreg::ST_BF16)

@@ -1,0 +1,4 @@
+// Kernel instantiations for f16 population storage.
+#include "oreg_kernels.cuh"
+
+OREG_DEFINE_LAUNCHERS(f16, oreg::ST_F16)

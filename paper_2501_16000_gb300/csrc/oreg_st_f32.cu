@@ -1,0 +1,4 @@
+// Kernel instantiations for f32 population storage.
+#include "oreg_kernels.cuh"
+
+OREG_DEFINE_LAUNCHERS(f32, oreg::ST_F32)

@@ -1,0 +1,4 @@
+// Kernel instantiations for f64 population storage.
+#include "oreg_kernels.cuh"
+
+OREG_DEFINE_LAUNCHERS(f64, oreg::ST_F64)

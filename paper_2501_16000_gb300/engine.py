@@ -1,0 +1,181 @@
+"""Python-level ``Lattice`` over the C ABI (include/oreg.h).
+
+PyTorch provides the device memory (the population buffer) and the CUDA
+stream; all computation happens in liboreg.so.  Host arrays are numpy float64.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import binding as B
+
+EQ = {"guided": B.OLB_EQ_GUIDED, "poly2": B.OLB_EQ_POLY2}
+COLL = {"oreg": B.OLB_COLL_OREG, "bgk": B.OLB_COLL_BGK}
+STORAGE = {"f64": B.OLB_F64, "f32": B.OLB_F32, "f16": B.OLB_F16_SHIFTED,
+           "bf16": B.OLB_BF16_SHIFTED}
+LAYOUT = {"ab": B.OLB_LAYOUT_AB, "aa": B.OLB_LAYOUT_AA}
+ELEM_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+def bytes_per_node_step(storage: str) -> int:
+    """Algorithmic HBM traffic of one node update: 9 reads + 9 writes."""
+    return 18 * ELEM_BYTES[storage]
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(nx, ny, tau, theta=1.0 / 3.0, eq="guided", coll="oreg", storage="f32",
+                layout="ab", rho0=1.0, device_buffer=0, buffer_bytes=0, stream=0):
+    return B.olb_params(int(nx), int(ny), float(tau), float(theta), float(rho0), EQ[eq],
+                        COLL[coll], STORAGE[storage], LAYOUT[layout], device_buffer or None,
+                        int(buffer_bytes), stream or None)
+
+
+def required_bytes(**kw) -> int:
+    p = make_params(**kw)
+    return int(B.load().olb_required_bytes(ctypes.byref(p)))
+
+
+class Lattice:
+    """One periodic D2Q9 lattice advanced by the OReg (or BGK) update.
+
+    ``torch_memory=True`` places the populations in a torch CUDA tensor and
+    runs on torch's current stream (the default when torch sees a GPU)."""
+
+    def __init__(self, nx, ny, tau, theta=1.0 / 3.0, eq="guided", coll="oreg",
+                 storage="f32", layout="ab", rho0=1.0, torch_memory=None, stream=None):
+        self.nx, self.ny, self.tau, self.theta = int(nx), int(ny), float(tau), float(theta)
+        self.eq, self.coll, self.storage, self.layout = eq, coll, storage, layout
+        self._buf = None
+        self._handle = None
+        kw = dict(nx=nx, ny=ny, tau=tau, theta=theta, eq=eq, coll=coll, storage=storage,
+                  layout=layout, rho0=rho0)
+        dev_ptr, nbytes, sptr = 0, 0, 0
+        if torch_memory is None:
+            try:
+                import torch
+                torch_memory = torch.cuda.is_available()
+            except ImportError:
+                torch_memory = False
+        if torch_memory:
+            import torch
+            nbytes = required_bytes(**kw)
+            if nbytes == 0:
+                p = make_params(**kw)
+                h = ctypes.c_void_p()
+                B.check(B.load().olb_create_lattice(ctypes.byref(p), ctypes.byref(h)),
+                        "olb_create_lattice")
+            self._buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            dev_ptr = self._buf.data_ptr()
+            s = stream if stream is not None else torch.cuda.current_stream()
+            self._torch_stream = s
+            sptr = s.cuda_stream
+        self.params = make_params(**kw, device_buffer=dev_ptr, buffer_bytes=nbytes, stream=sptr)
+        h = ctypes.c_void_p()
+        B.check(B.load().olb_create_lattice(ctypes.byref(self.params), ctypes.byref(h)),
+                "olb_create_lattice")
+        self._handle = h
+
+    # -- lifetime ---------------------------------------------------------
+    @property
+    def handle(self):
+        if self._handle is None:
+            raise RuntimeError("lattice is closed")
+        return self._handle
+
+    def close(self) -> None:
+        if self._handle is not None:
+            st = B.load().olb_destroy(self._handle)
+            self._handle = None
+            self._buf = None
+            B.check(st, "olb_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self._handle is not None:
+                B.load().olb_destroy(self._handle)
+                self._handle = None
+        except Exception:
+            pass
+
+    # -- state --------------------------------------------------------------
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def time(self) -> int:
+        return int(B.load().olb_time(self.handle))
+
+    def set_option(self, option: int, value: int) -> None:
+        B.call("olb_set_option", self.handle, int(option), int(value))
+
+    def init_shear_wave(self, rho0=1.0, u0=0.05, m=1, n=0) -> None:
+        B.call("olb_init_shear_wave", self.handle, float(rho0), float(u0), int(m), int(n))
+
+    def init_shock_tube(self, rho_left=1.5, rho_right=0.75, x_split=None) -> None:
+        xs = self.nx // 2 if x_split is None else int(x_split)
+        B.call("olb_init_shock_tube", self.handle, float(rho_left), float(rho_right), xs)
+
+    def init_fields(self, rho, ux, uy) -> None:
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy)]
+        for a in arrs:
+            assert a.shape == (self.ny, self.nx)
+        B.call("olb_init_fields", self.handle, *[_dptr(a) for a in arrs])
+
+    def init_case(self, case) -> None:
+        """Initial condition of a ``workloads.LatticeCase``."""
+        if case.case == "shear":
+            self.init_shear_wave(case.rho0, case.u0, case.m, case.n)
+        else:
+            self.init_shock_tube(case.rho_left, case.rho_right, case.x_split)
+
+    def step(self, n: int = 1) -> None:
+        B.call("olb_step", self.handle, int(n))
+
+    def moments(self, theta_loc: bool = False):
+        rho, ux, uy = (np.empty((self.ny, self.nx)) for _ in range(3))
+        th = np.empty((self.ny, self.nx)) if theta_loc else None
+        B.call("olb_moments", self.handle, _dptr(rho), _dptr(ux), _dptr(uy),
+               _dptr(th) if th is not None else None)
+        return (rho, ux, uy, th) if theta_loc else (rho, ux, uy)
+
+    def populations(self) -> np.ndarray:
+        f = np.empty((9, self.ny, self.nx))
+        B.call("olb_get_populations", self.handle, _dptr(f))
+        return f
+
+    def region(self, x0: int, y0: int, wx: int, wy: int) -> np.ndarray:
+        """Canonical populations of a window, shape (9, wy, wx)."""
+        f = np.empty((9, wy, wx))
+        B.call("olb_get_region", self.handle, int(x0), int(y0), int(wx), int(wy), _dptr(f))
+        return f
+
+    def set_populations(self, f, t: int = 0) -> None:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9, self.ny, self.nx)
+        B.call("olb_set_populations", self.handle, _dptr(f), int(t))
+
+    def diagnostics(self, raise_nonfinite: bool = True):
+        m, jx, jy = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        nf = ctypes.c_int64()
+        st = B.load().olb_diagnostics(self.handle, ctypes.byref(m), ctypes.byref(jx),
+                                      ctypes.byref(jy), ctypes.byref(nf))
+        if st != B.OLB_ERR_NONFINITE or raise_nonfinite:
+            B.check(st, "olb_diagnostics")
+        return {"mass": m.value, "mom_x": jx.value, "mom_y": jy.value, "nonfinite": nf.value}
+
+    def wave_amplitude(self, m: int, n: int) -> float:
+        a = ctypes.c_double()
+        B.call("olb_wave_amplitude", self.handle, int(m), int(n), ctypes.byref(a))
+        return a.value

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA stream-collide path (through the C ABI) against the
+FP64 CPU oracle, element by element on the canonical populations.
+
+Tolerances (relative L_inf over all 9 populations, normalised by max |f|):
+FP64 1e-12 and FP32 1e-5 after the stated step counts; the half-precision
+storage formats are checked against bounds derived from their unit roundoff
+(see test docstrings)."""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_16000_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_16000_gb300 import build
+    build.build()
+
+
+def _oracle_params(case):
+    return O.params(case.nx, case.ny, case.tau, case.theta,
+                    O.GUIDED if case.eq == "guided" else O.POLY2,
+                    O.OREG if case.coll == "oreg" else O.BGK)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(case, steps):
+    p = _oracle_params(case)
+    f0 = O.init_equilibrium(p, *case.fields())
+    return O.run(f0, p, steps)
+
+
+def gpu_run(case, steps, storage, layout, split=None):
+    from paper_2501_16000_gb300.engine import Lattice
+    with Lattice(case.nx, case.ny, case.tau, case.theta, case.eq, case.coll, storage,
+                 layout) as lat:
+        lat.init_case(case)
+        if split:
+            for k in split:
+                lat.step(k)
+        else:
+            lat.step(steps)
+        assert lat.time == steps
+        return lat.populations()
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+CONFIG1 = [W.shear_64("oreg"), W.shear_64("bgk"), W.shear_64("oreg", 1, 1)]
+CONFIG2 = [W.shock_2048x4("guided"), W.shock_2048x4("poly2")]
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("case", CONFIG1, ids=lambda c: f"shear64-{c.coll}-{c.m}{c.n}")
+def test_config1_shear_wave_fp64(case, layout):
+    err = rel_linf(gpu_run(case, case.steps, "f64", layout), oracle_run(case, case.steps))
+    assert err <= TOL["f64"], err
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("case", CONFIG2, ids=lambda c: f"shock-{c.eq}")
+def test_config2_shock_tube_fp64(case, layout):
+    err = rel_linf(gpu_run(case, case.steps, "f64", layout), oracle_run(case, case.steps))
+    assert err <= TOL["f64"], err
+
+
+@pytest.mark.parametrize("case", CONFIG1[:2], ids=lambda c: f"shear64-{c.coll}")
+def test_config1_shear_wave_fp32(case):
+    err = rel_linf(gpu_run(case, case.steps, "f32", "ab"), oracle_run(case, case.steps))
+    assert err <= TOL["f32"], err
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("case", CONFIG2, ids=lambda c: f"shock-{c.eq}")
+def test_config2_shock_tube_fp32(case, layout):
+    err = rel_linf(gpu_run(case, case.steps, "f32", layout), oracle_run(case, case.steps))
+    print(f"FP32 shock {case.eq} {layout}: rel Linf {err:.3e}")
+    assert err <= TOL["f32"], err
+
+
+def test_theta_off_reference_fp64():
+    case = W.LatticeCase(nx=48, ny=40, tau=0.6, theta=0.3, case="shear", u0=0.05, m=2, n=1)
+    err = rel_linf(gpu_run(case, 300, "f64", "aa"), oracle_run(case, 300))
+    assert err <= TOL["f64"], err
+
+
+# ---------------------------------------------------------------------------
+# ragged sizes, odd and even step counts, random non-equilibrium states
+# ---------------------------------------------------------------------------
+
+def random_state(nx, ny, eq, theta, seed):
+    """Equilibrium of a random smooth-ish field plus a random non-equilibrium
+    part, all positive."""
+    rng = np.random.default_rng(seed)
+    p = O.params(nx, ny, 0.7, theta, O.GUIDED if eq == "guided" else O.POLY2, O.OREG)
+    rho = 1.0 + 0.1 * rng.uniform(-1, 1, (ny, nx))
+    ux = 0.08 * rng.uniform(-1, 1, (ny, nx))
+    uy = 0.08 * rng.uniform(-1, 1, (ny, nx))
+    f = O.init_equilibrium(p, rho, ux, uy)
+    return f * (1.0 + 0.02 * rng.uniform(-1, 1, f.shape))
+
+
+SIZES = [(1, 1), (1, 5), (5, 1), (3, 2), (37, 23), (131, 7), (257, 3), (520, 4)]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("nx,ny", SIZES)
+def test_ragged_random_states(nx, ny, layout, storage):
+    from paper_2501_16000_gb300.engine import Lattice
+    for eq, coll, theta in (("guided", "oreg", 0.35), ("poly2", "bgk", 1.0 / 3.0)):
+        f0 = random_state(nx, ny, eq, theta, seed=nx * 1000 + ny)
+        p = O.params(nx, ny, 0.7, theta, O.GUIDED if eq == "guided" else O.POLY2,
+                     O.OREG if coll == "oreg" else O.BGK)
+        with Lattice(nx, ny, 0.7, theta, eq, coll, storage, layout) as lat:
+            lat.set_populations(f0, 0)
+            ref = f0
+            for steps in (1, 1, 5, 2):      # even and odd times, AA parity both ways
+                lat.step(steps)
+                ref = O.run(ref, p, steps)
+                err = rel_linf(lat.populations(), ref)
+                assert err <= TOL[storage] * (1 if storage == "f64" else 0.1), \
+                    (eq, coll, lat.time, err)
+
+
+@pytest.mark.parametrize("storage,bound", [("f16", 2e-3), ("bf16", 1.6e-2)])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_half_precision_storage_short_runs(storage, bound, layout):
+    """Shifted half storage: each step rounds g = f - s to 11 (f16) or 8 (bf16)
+    significant bits, |g| <= ~0.15 here, so a few steps stay within a few
+    half-ulps of max|g| relative to max|f| (bound = 4 ulp * 0.15 / 0.44)."""
+    from paper_2501_16000_gb300.engine import Lattice
+    nx, ny = 131, 7
+    f0 = random_state(nx, ny, "guided", 1.0 / 3.0, seed=3)
+    p = O.params(nx, ny, 0.7, 1.0 / 3.0, O.GUIDED, O.OREG)
+    with Lattice(nx, ny, 0.7, storage=storage, layout=layout) as lat:
+        lat.set_populations(f0, 0)
+        lat.step(3)
+        err = rel_linf(lat.populations(), O.run(f0, p, 3))
+    assert err <= bound, err
+
+
+# ---------------------------------------------------------------------------
+# state plumbing: round trips, checkpoint/resume, moments, diagnostics
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_set_get_roundtrip(storage, layout):
+    from paper_2501_16000_gb300.engine import Lattice
+    f0 = random_state(37, 11, "guided", 1.0 / 3.0, seed=1)
+    with Lattice(37, 11, 0.8, storage=storage, layout=layout) as lat:
+        for t in (0, 1):           # even and odd AA parity
+            lat.set_populations(f0, t)
+            got = lat.populations()
+            if storage == "f64":
+                assert np.array_equal(got, f0)
+            else:
+                eps = {"f32": 2 ** -24, "f16": 2 ** -11, "bf16": 2 ** -8}[storage]
+                assert np.abs(got - f0).max() <= eps * 0.5 + 1e-12
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_checkpoint_resume_is_bitwise(layout):
+    from paper_2501_16000_gb300.engine import Lattice
+    case = W.shear_64("oreg")
+    with Lattice(64, 64, case.tau, storage="f32", layout=layout) as a:
+        a.init_case(case)
+        a.step(37)
+        ck = a.populations()
+        a.step(20)
+        straight = a.populations()
+    with Lattice(64, 64, case.tau, storage="f32", layout=layout) as b:
+        b.set_populations(ck, 37)
+        b.step(20)
+        assert np.array_equal(b.populations(), straight)
+
+
+def test_moments_and_diagnostics_match_oracle():
+    from paper_2501_16000_gb300.engine import Lattice
+    case = W.shear_64("oreg")
+    ref = oracle_run(case, 100)
+    rho_o, ux_o, uy_o, th_o = O.fields(ref)
+    with Lattice(64, 64, case.tau, storage="f64", layout="aa") as lat:
+        lat.init_case(case)
+        lat.step(100)
+        rho, ux, uy, th = lat.moments(theta_loc=True)
+        d = lat.diagnostics()
+        amp = lat.wave_amplitude(case.m, case.n)
+    for a, b in ((rho, rho_o), (ux, ux_o), (uy, uy_o), (th, th_o)):
+        assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(b).max())
+    assert abs(d["mass"] - rho_o.sum()) <= 1e-11
+    assert abs(d["mom_x"] - (rho_o * ux_o).sum()) <= 1e-11
+    assert d["nonfinite"] == 0
+    s = np.sin(2 * np.pi * W.shear_wave_phase(64, 64, case.m, case.n))
+    ex, ey = W.shear_wave_direction(64, 64, case.m, case.n)
+    amp_o = 2.0 / 4096 * np.sum((ux_o * ex + uy_o * ey) * s)
+    assert abs(amp - amp_o) <= 1e-12
+
+
+def test_init_fields_matches_analytic_init():
+    from paper_2501_16000_gb300.engine import Lattice
+    case = W.shear_64("oreg")
+    with Lattice(64, 64, case.tau, storage="f64") as a, Lattice(64, 64, case.tau, storage="f64") as b:
+        a.init_case(case)
+        b.init_fields(*case.fields())
+        assert rel_linf(a.populations(), b.populations()) <= 1e-15
+
+
+def test_mass_conservation_fp64():
+    from paper_2501_16000_gb300.engine import Lattice
+    case = W.shock_2048x4()
+    with Lattice(case.nx, case.ny, case.tau, storage="f64", layout="aa") as lat:
+        lat.init_case(case)
+        m0 = lat.diagnostics()["mass"]
+        lat.step(1000)
+        d = lat.diagnostics()
+    assert abs(d["mass"] / m0 - 1) <= 1e-13
+    assert abs(d["mom_y"]) <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# error paths made on the host (no GPU fault)
+# ---------------------------------------------------------------------------
+
+def test_error_paths():
+    from paper_2501_16000_gb300 import binding as B
+    from paper_2501_16000_gb300.engine import Lattice
+    lat = Lattice(16, 8, 0.8, storage="f32")
+    with pytest.raises(B.OregError) as e:
+        lat.step(1)                      # before any init
+    assert e.value.status == B.OLB_ERR_STATE
+    lat.init_shear_wave(1.0, 0.05, 1, 0)
+    with pytest.raises(B.OregError) as e:
+        lat.step(-1)
+    assert e.value.status == B.OLB_ERR_INVALID
+    f = lat.populations()
+    f[3, 2, 5] = np.nan                  # a non-finite value injected from the host
+    lat.set_populations(f, 4)
+    with pytest.raises(B.OregError) as e:
+        lat.diagnostics()
+    assert e.value.status == B.OLB_ERR_NONFINITE
+    assert lat.diagnostics(raise_nonfinite=False)["nonfinite"] == 1
+    lat.close()
