@@ -166,7 +166,7 @@ StateGeom geom(const olb_lattice *L) {
     g.ny = L->p.ny;
     g.pitch = L->pitch;
     g.plane = L->plane;
-    g.aa_odd = (L->p.layout == OLB_LAYOUT_AA) && (L->t & 1);
+    g.mode = L->p.layout == OLB_LAYOUT_AB ? STATE_AB : ((L->t & 1) ? STATE_AA_ODD : STATE_AA_EVEN);
     return g;
 }
 

@@ -10,9 +10,11 @@
 namespace oreg {
 
 // ---------------------------------------------------------------------------
-// Stream-collide, A-B layout: pull the 9 populations of 32*V nodes per warp
-// from src (streaming of Eqs. 1/7 as a gather f_i(x - c_i)), collide, store
-// to dst at the node's own position.
+// Stream-collide, A-B layout.  A buffer holds post-collision populations at
+// the node that produced them.  A warp gathers, for 32*V nodes of one row,
+// f_i(x) = post_i(x - c_i) from src (the streaming of Eqs. 1/7 as a pull),
+// which is the pre-collision state S_t(x); it collides and stores post(x) to
+// dst at x.
 // ---------------------------------------------------------------------------
 template <int S, int I, bool AA_ODD>
 __device__ __forceinline__ void pull_plane(const typename Storage<S>::T *base, size_t plane,
@@ -181,17 +183,20 @@ __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, 
 
 // ---------------------------------------------------------------------------
 // Canonical-state access (layout and parity aware), FP64.
-// S_t(x)_i = base[i][y][x] + s_i, except on odd AA steps where it is
-// base[opp(i)][y - c_iy][x - c_ix] + s_i.
+//   A-B: the buffer holds the post-collision populations of the previous step
+//        at the node where they were produced (the pull kernel gathers them
+//        along -c_i before colliding), so S_t(x)_i = buf[i][x - c_i] + s_i.
+//   AA, even t: S_t(x)_i = buf[i][x] + s_i.
+//   AA, odd t:  S_t(x)_i = buf[opp(i)][x - c_i] + s_i.
 // ---------------------------------------------------------------------------
 template <int S>
-__device__ __forceinline__ size_t canon_index(int i, int x, int y, int nx, int ny, int pitch,
-                                              size_t plane, int aa_odd) {
-    if (!aa_odd) return i * plane + (size_t)y * pitch + x;
+__device__ __forceinline__ size_t canon_index(int i, int x, int y, const StateGeom &g) {
+    if (g.mode == STATE_AA_EVEN) return i * g.plane + (size_t)y * g.pitch + x;
     int xs = x - cx_of(i), ys = y - cy_of(i);
-    xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-    ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-    return opp_of(i) * plane + (size_t)ys * pitch + xs;
+    xs = xs < 0 ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
+    ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+    const int p = g.mode == STATE_AA_ODD ? opp_of(i) : i;
+    return p * g.plane + (size_t)ys * g.pitch + xs;
 }
 
 template <int S>
@@ -200,8 +205,7 @@ __device__ __forceinline__ void canon_node(const typename Storage<S>::T *base, i
                                            double f[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const size_t idx = canon_index<S>(i, x, y, g.nx, g.ny, g.pitch, g.plane, g.aa_odd);
-        f[i] = (double)Storage<S>::dec(base[idx]) + shift[i];
+        f[i] = (double)Storage<S>::dec(base[canon_index<S>(i, x, y, g)]) + shift[i];
     }
 }
 
@@ -230,7 +234,7 @@ __device__ __forceinline__ void eq_dev_f64(double rho, double ux, double uy,
     }
 }
 
-// S_0 = f^eq(rho(x), u(x)) written in canonical position (t = 0 is even).
+// S_0 = f^eq(rho(x), u(x)) written where the layout keeps S_0(x)_i.
 template <int S, int EQ>
 __global__ void k_init(typename Storage<S>::T *base, StateGeom g, InitSpec spec,
                        const CollConst<double> kd) {
@@ -260,8 +264,7 @@ __global__ void k_init(typename Storage<S>::T *base, StateGeom g, InitSpec spec,
     eq_dev_f64<EQ>(rho, ux, uy, kd, geq);
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        base[i * g.plane + (size_t)y * g.pitch + x] =
-            Storage<S>::enc((typename Storage<S>::C)geq[i]);
+        base[canon_index<S>(i, x, y, g)] = Storage<S>::enc((typename Storage<S>::C)geq[i]);
 }
 
 // Canonical populations of the window [x0, x0 + wx) x [y0, y0 + wy) into
@@ -289,8 +292,8 @@ __global__ void k_set_canonical(typename Storage<S>::T *base, StateGeom g, int y
     const int y = y0 + (int)(n / g.nx), x = (int)(n % g.nx);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const size_t idx = canon_index<S>(i, x, y, g.nx, g.ny, g.pitch, g.plane, g.aa_odd);
-        base[idx] = Storage<S>::enc((typename Storage<S>::C)(in[i * cnt + n] - kd.shift[i]));
+        base[canon_index<S>(i, x, y, g)] =
+            Storage<S>::enc((typename Storage<S>::C)(in[i * cnt + n] - kd.shift[i]));
     }
 }
 

@@ -10,13 +10,15 @@ namespace oreg {
 
 template <typename C> struct CollConst;
 
+// Where a layout keeps the canonical state S_t (see canon_index).
+enum { STATE_AB = 0, STATE_AA_EVEN = 1, STATE_AA_ODD = 2 };
+
 // Geometry of a population state: planes of ny rows of `pitch` elements; the
-// first nx elements of a row are nodes, the rest padding.  aa_odd selects the
-// odd-step addressing of the in-place layout.
+// first nx elements of a row are nodes, the rest padding.
 struct StateGeom {
     int nx, ny, pitch;
     size_t plane;  // elements per population plane
-    int aa_odd;
+    int mode;      // STATE_*
 };
 
 struct StepArgs {
