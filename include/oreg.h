@@ -179,6 +179,46 @@ olb_status olb_diagnostics(olb_lattice *lat, double *mass, double *mom_x, double
  * the decay statistic of Sec. IV.  Synchronises the stream. */
 olb_status olb_wave_amplitude(olb_lattice *lat, int32_t m, int32_t n, double *amp);
 
+/* Largest ny olb_diagnostics_noalloc accepts. */
+#define OLB_NOALLOC_MAX_ROWS 16384
+
+/* olb_diagnostics for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is plumbing for embedding the library.
+ *
+ * Some callers own the GPU memory budget themselves and must not let a
+ * library call cudaMalloc: a serving loop that admits work against an HBM
+ * budget it accounts for byte by byte, or a host loop on a latency budget in
+ * which cudaMalloc/cudaFree would add device-wide synchronisation.  Such a
+ * caller keeps the populations in its own device buffer and still needs the
+ * mass, momentum and non-finite count.  This call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  Its reduction
+ * scratch is a fixed static device array of OLB_NOALLOC_MAX_ROWS x 4 doubles
+ * (512 KiB) that every GPU which loads liboreg.so holds until the process
+ * exits.
+ *
+ * d_populations: device memory laid out exactly as a lattice created with
+ *   the same olb_params keeps it (the device_buffer of olb_create_lattice,
+ *   olb_required_bytes(p) bytes, 16-byte aligned).
+ * p: nx, ny, tau, theta, rho0, eq, storage, layout and cuda_stream describe
+ *   that state; device_buffer and buffer_bytes are ignored.  ny must not
+ *   exceed OLB_NOALLOC_MAX_ROWS (larger lattices are rejected with
+ *   OLB_ERR_INVALID).
+ * t: the time of the state (selects the A-B buffer and the AA parity).
+ * d_out: device double[4] receiving total mass, momentum x, momentum y and
+ *   the number of nodes holding a non-finite population.
+ *
+ * Asynchronous on p->cuda_stream (NULL: the legacy default stream); the
+ * caller synchronises before reading d_out.  Results equal olb_diagnostics
+ * up to the order of the FP64 additions.  The first call on a device looks
+ * up the device address of the static array (with that device current);
+ * make that first call before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU race and must be ordered by
+ * the caller.  Every partial the call reads is written by the same call, so
+ * the array needs no clearing between calls.  On failure the message is
+ * available from olb_last_error(). */
+olb_status olb_diagnostics_noalloc(const void *d_populations, const olb_params *p, int64_t t,
+                                   double *d_out);
+
 /* Releases the lattice and everything it allocated (NULL is a no-op).
  * Waits for the lattice's pending work first. */
 olb_status olb_destroy(olb_lattice *lat);

@@ -72,6 +72,8 @@ SIGNATURES = {
     "olb_set_populations": (ctypes.c_int, [_h, _d, ctypes.c_int64]),
     "olb_diagnostics": (ctypes.c_int, [_h, _d, _d, _d, _P(ctypes.c_int64)]),
     "olb_wave_amplitude": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32, _d]),
+    "olb_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, _P(olb_params), ctypes.c_int64,
+                                               ctypes.c_void_p]),
     "olb_destroy": (ctypes.c_int, [_h]),
     "olb_last_error": (ctypes.c_char_p, []),
 }

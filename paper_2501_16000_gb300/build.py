@@ -30,6 +30,7 @@ UNITS = {
     "oreg_st_f16.cu": [],
     "oreg_st_bf16.cu": [],
     "oreg_batch.cu": [],
+    "oreg_noalloc.cu": [],
 }
 
 

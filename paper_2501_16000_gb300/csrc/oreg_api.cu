@@ -57,6 +57,12 @@ int vec_elems(int storage) { return 16 / (int)elem_size(storage); }
 constexpr size_t CHUNK_BYTES_MAX = size_t(64) << 20;  // readback scratch
 }  // namespace
 
+namespace oreg {
+// Records the message of a failed call made outside this file (the
+// no-allocation diagnostics entry point) for olb_last_error().
+void set_last_error_message(const char *msg) { g_last_error = msg; }
+}  // namespace oreg
+
 struct olb_lattice {
     olb_params p;
     int V;
