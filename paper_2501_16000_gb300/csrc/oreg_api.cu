@@ -124,20 +124,31 @@ size_t pop_bytes(const olb_params *p) {
     return (size_t)nbuf * 9 * plane * elem_size(p->storage);
 }
 
-// Constants of the collision for the compute type C; the shift is the rest
-// equilibrium w_i rho0 rounded to C and corr the exact remainder.
+// hi + lo split of a double into the compute type C: hi = (C)v and lo the
+// remainder, so that hi + lo represents v to ~2^-48 in FP32.
+template <typename C>
+void split(double v, C &hi, C &lo) {
+    hi = (C)v;
+    lo = (C)(v - (double)hi);
+}
+
+// Constants of the collision for the compute type C.  The storage shift s_i
+// is the rest equilibrium w_i rho0 rounded to C and corr_i the exact
+// remainder w_i rho0 - s_i; the rest factors and weights are kept as hi + lo
+// pairs (see collide()).
 template <typename C>
 CollConst<C> make_const(const olb_params *p) {
     CollConst<C> k;
     const double th = p->eq == OLB_EQ_GUIDED ? p->theta : 1.0 / 3.0;
     const double psi0[3] = {1.0 - th, 0.5 * th, 0.5 * th};
     double corr_sum = 0.0;
-    for (int a = 0; a < 3; ++a) k.psi0[a] = (C)psi0[a];
+    for (int a = 0; a < 3; ++a) split<C>(psi0[a], k.psi0[a], k.psi0_lo[a]);
     for (int i = 0; i < 9; ++i) {
-        const double w = psi0[kidx(cx_of(i))] * psi0[kidx(cy_of(i))];
+        const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
+        const double w = psi0[a] * psi0[b];
+        split<C>(w, k.w[i], k.w_lo[i]);
         const C s = (C)(w * p->rho0);
         const double corr = w * p->rho0 - (double)s;
-        k.w[i] = (C)w;
         k.shift[i] = s;
         k.corr[i] = (C)corr;
         corr_sum += corr;
@@ -150,7 +161,8 @@ CollConst<C> make_const(const olb_params *p) {
     return k;
 }
 
-// FP64 constants whose shift is exactly the stored format's shift.
+// FP64 constants (initialisation and readback) whose shift is exactly the
+// stored format's shift.
 CollConst<double> make_const_f64_for(const olb_params *p) {
     CollConst<double> kd = make_const<double>(p);
     if (p->storage != OLB_F64) {

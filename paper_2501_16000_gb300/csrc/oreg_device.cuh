@@ -92,8 +92,10 @@ __device__ __forceinline__ void st_vec(typename Storage<S>::T *p, const Vec<S> &
 template <typename C> struct CollConst {
     C rho0;          // reference density of the shift
     C psi0[3];       // 1-D rest factors: guided Psi_0(0) = 1 - theta, Psi_+-(0) = theta/2;
-                     // poly2 W_0 = 1 - theta0, W_+- = theta0 / 2
-    C w[9];          // W_i = psi0[a] psi0[b]
+                     // poly2 W_0 = 1 - theta0, W_+- = theta0 / 2; rounded to C ...
+    C psi0_lo[3];    // ... plus the rounding remainder (hi + lo exact to ~2^-48)
+    C w[9];          // W_i = Psi_a(0) Psi_b(0) rounded to C ...
+    C w_lo[9];       // ... plus the rounding remainder
     C shift[9];      // storage shift s_i (rest equilibrium rounded to C)
     C corr[9];       // W_i rho0 - s_i (exact difference, rounded to C)
     C sum_corr;      // sum_i corr_i
@@ -171,15 +173,26 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
     const C ux = jx * inv_rho, uy = jy * inv_rho;
     const C ux2 = ux * ux, uy2 = uy * uy;
 
+    // The equilibrium constants enter in hi + lo form.  Rounded to C alone
+    // they would break sum_b Psi_b(0) = 1 and sum_i W_i c_i c_i = theta by a
+    // unit roundoff, which acts as a small mass and momentum source on every
+    // node at every step; in FP32 that bias, not random rounding, dominates
+    // the drift from the FP64 result over thousands of steps.
     C geq[9];
     if constexpr (EQ == EQ_GUIDED) {
-        const C dpx[3] = {-ux2, C(0.5) * (ux + ux2), C(0.5) * (ux2 - ux)};
-        const C dpy[3] = {-uy2, C(0.5) * (uy + uy2), C(0.5) * (uy2 - uy)};
+        // dPsi_+- = u^2/2 +- u/2, dPsi_0 = -u^2 (u/2 and u^2/2 are exact halvings)
+        const C qx = C(0.5) * ux, hx = C(0.5) * ux2, qy = C(0.5) * uy, hy = C(0.5) * uy2;
+        const C dpx[3] = {-ux2, hx + qx, hx - qx};
+        const C dpy[3] = {-uy2, hy + qy, hy - qy};
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
+            // dPsi_a Psi_b + Psi_a(0) dPsi_b with Psi(0) = hi + lo
             const C psib = k.psi0[b] + dpy[b];
-            geq[i] = fma(drho, k.w[i], fma(rho, fma(dpx[a], psib, k.psi0[a] * dpy[b]), k.corr[i]));
+            const C t = fma(dpx[a], psib,
+                            fma(dpx[a], k.psi0_lo[b], fma(k.psi0[a], dpy[b], k.psi0_lo[a] * dpy[b])));
+            const C vel = fma(rho, t, k.corr[i]);
+            geq[i] = fma(drho, k.w[i], fma(drho, k.w_lo[i], vel));
         }
     } else {
         const C u2 = ux2 + uy2;
@@ -187,7 +200,9 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         for (int i = 0; i < 9; ++i) {
             const C cu = C(cx_of(i)) * ux + C(cy_of(i)) * uy;
             const C poly = fma(C(3), cu, fma(C(4.5) * cu, cu, C(-1.5) * u2));
-            geq[i] = fma(k.w[i], fma(rho, poly, drho), k.corr[i]);
+            const C rp = rho * poly;
+            const C vel = fma(rp, k.w[i], fma(rp, k.w_lo[i], k.corr[i]));
+            geq[i] = fma(drho, k.w[i], fma(drho, k.w_lo[i], vel));
         }
     }
 

@@ -221,15 +221,16 @@ __device__ __forceinline__ void eq_dev_f64(double rho, double ux, double uy,
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
-            geq[i] = drho * k.w[i] + rho * (dpx[a] * (k.psi0[b] + dpy[b]) + k.psi0[a] * dpy[b]) +
-                     k.corr[i];
+            geq[i] = drho * (k.w[i] + k.w_lo[i]) +
+                     rho * (dpx[a] * (k.psi0[b] + dpy[b]) + k.psi0[a] * dpy[b]) + k.corr[i];
         }
     } else {
         const double u2 = ux2 + uy2;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const double cu = cx_of(i) * ux + cy_of(i) * uy;
-            geq[i] = k.w[i] * (drho + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2)) + k.corr[i];
+            geq[i] = (k.w[i] + k.w_lo[i]) * (drho + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2)) +
+                     k.corr[i];
         }
     }
 }

@@ -133,6 +133,7 @@ CollConst<double> noalloc_constants(const olb_params *p) {
         const double w = psi0[kidx(cx_of(i))] * psi0[kidx(cy_of(i))];
         const double s = p->storage == OLB_F64 ? w * p->rho0 : (double)(float)(w * p->rho0);
         k.w[i] = w;
+        k.w_lo[i] = 0.0;
         k.shift[i] = s;
         k.corr[i] = w * p->rho0 - s;
         corr_sum += k.corr[i];
