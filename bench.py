@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--theta", type=float, default=1.0 / 3.0)
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--layout", default="ab", choices=["ab", "aa"])
+    ap.add_argument("--comp", type=int, default=0, help="OLB_OPT_COMPENSATED (FP32)")
+    ap.add_argument("--warps", type=int, default=4, help="OLB_OPT_WARPS_PER_BLOCK")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-side", type=int, default=1024)
@@ -61,10 +63,14 @@ def measured_peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+STEP_KERNEL_SOURCES = ("oreg_device.cuh", "oreg_kernels.cuh")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources that define the stream-collide kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2501_16000_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in STEP_KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -237,6 +243,8 @@ def run_native(args):
     stream = torch.cuda.Stream()
     lat = Lattice(case.nx, case.ny, case.tau, case.theta, "guided", "oreg", args.storage,
                   args.layout, stream=stream)
+    lat.set_option(B.OLB_OPT_COMPENSATED, args.comp)
+    lat.set_option(B.OLB_OPT_WARPS_PER_BLOCK, args.warps)
     lat.init_case(case)
 
     def barrier():
@@ -330,6 +338,7 @@ def run_native(args):
                        "nodes": N, "theta": case.theta, "tau": case.tau, "u0": case.u0,
                        "wave": [case.m, case.n], "storage": args.storage,
                        "layout": args.layout, "diagnostics_every": DIAG_EVERY,
+                       "compensated": args.comp, "warps_per_block": args.warps,
                        "l2": f"inputs larger than L2 ({lat_bytes(args.storage, N) / 1e9:.1f} GB "
                              f"state vs 126 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

@@ -91,12 +91,13 @@ typedef struct {
 /* Tuning and precision options of a lattice (olb_set_option). */
 typedef enum {
     /* 1: accumulate the conserved moments (mass, momentum) of the FP32
-       collision with error-free (TwoSum) additions, which keeps FP32 rounding
-       out of the conserved quantities; 0: plain sums.  Default 1 for
-       OLB_F32, ignored by the other formats. */
+       collision with error-free (TwoSum) additions, which keeps their FP32
+       rounding out of long runs (about half the drift from FP64 on a
+       weakly damped shock tube) at ~13% of the FP32 kernel's throughput;
+       0 (default): plain sums.  Ignored by the other formats. */
     OLB_OPT_COMPENSATED = 1,
     /* warps per thread block of the stream-collide kernels: 1, 2, 4 or 8
-       (default 8).  Each warp updates 32*V consecutive nodes of one row,
+       (default 4).  Each warp updates 32*V consecutive nodes of one row,
        V = 16 bytes / element size. */
     OLB_OPT_WARPS_PER_BLOCK = 2
 } olb_option;

@@ -84,6 +84,9 @@ struct olb_lattice {
     int red_blocks;
     void *d_chunk;        // readback scratch (lazy)
     size_t chunk_bytes;
+    double *d_tab;        // shear-mode sin/cos tables (lazy), for (tab_m, tab_n)
+    double *h_tab;
+    int tab_m, tab_n;
     CollConst<double> kd;     // FP64 constants (shift as stored type's shift)
     CollConst<float> kf;      // FP32 constants (F32, F16, BF16 compute)
 };
@@ -254,6 +257,44 @@ olb_status reduce(olb_lattice *L, const ModeSpec &mode, double out[RED_QUANTITIE
              "copying reduction result");
     OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising reduction");
     for (int q = 0; q < RED_QUANTITIES; ++q) out[q] = L->h_red[q];
+    // the kernel sums the shifted values g; add the shifts of the finite nodes
+    double sum_shift = 0.0;
+    for (int i = 0; i < 9; ++i) sum_shift += L->kd.shift[i];
+    const double n_finite = (double)L->p.nx * L->p.ny - out[3];
+    out[0] += n_finite * sum_shift;
+    return OLB_OK;
+}
+
+// FP64 tables sin/cos(2 pi m x / nx) and sin/cos(2 pi n y / ny) for the
+// mode projection, rebuilt when (m, n) changes.
+olb_status mode_tables(olb_lattice *L, int m, int n) {
+    const size_t cnt = 2 * ((size_t)L->p.nx + L->p.ny);
+    if (!L->d_tab) {
+        OLB_CUDA(cudaMalloc(&L->d_tab, cnt * sizeof(double)), "allocating mode tables");
+        OLB_CUDA(cudaMallocHost(&L->h_tab, cnt * sizeof(double)), "allocating mode tables");
+        L->tab_m = L->tab_n = 0;
+    } else if (L->tab_m == m && L->tab_n == n) {
+        return OLB_OK;
+    }
+    const int nx = L->p.nx, ny = L->p.ny;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int x = 0; x < nx; ++x) {
+        const long long r = ((long long)m * x) % nx;
+        const double a = two_pi * (double)(r < 0 ? r + nx : r) / nx;
+        L->h_tab[x] = std::sin(a);
+        L->h_tab[nx + x] = std::cos(a);
+    }
+    for (int y = 0; y < ny; ++y) {
+        const long long r = ((long long)n * y) % ny;
+        const double b = two_pi * (double)(r < 0 ? r + ny : r) / ny;
+        L->h_tab[2 * nx + y] = std::sin(b);
+        L->h_tab[2 * nx + ny + y] = std::cos(b);
+    }
+    OLB_CUDA(cudaMemcpyAsync(L->d_tab, L->h_tab, cnt * sizeof(double), cudaMemcpyHostToDevice,
+                             L->stream),
+             "copying mode tables");
+    L->tab_m = m;
+    L->tab_n = n;
     return OLB_OK;
 }
 
@@ -290,8 +331,8 @@ olb_status olb_create_lattice(const olb_params *p, olb_lattice **out) {
     L->buf_elems = 9 * L->plane;
     L->nbuf = p->layout == OLB_LAYOUT_AB ? 2 : 1;
     L->t = -1;
-    L->comp = p->storage == OLB_F32 ? 1 : 0;
-    L->warps_per_block = 8;
+    L->comp = 0;
+    L->warps_per_block = 4;
     L->kd = make_const_f64_for(p);
     L->kf = make_const<float>(p);
 
@@ -615,6 +656,9 @@ olb_status olb_wave_amplitude(olb_lattice *L, int32_t m, int32_t n, double *amp)
     const double nk = std::hypot(kx, ky);
     mode.ex = -ky / nk;
     mode.ey = kx / nk;
+    st = mode_tables(L, m, n);
+    if (st != OLB_OK) return st;
+    mode.tab = L->d_tab;
     double r[RED_QUANTITIES];
     st = reduce(L, mode, r);
     if (st != OLB_OK) return st;
@@ -634,6 +678,8 @@ olb_status olb_destroy(olb_lattice *L) {
     if (L->d_red) cudaFree(L->d_red);
     if (L->h_red) cudaFreeHost(L->h_red);
     if (L->d_chunk) cudaFree(L->d_chunk);
+    if (L->d_tab) cudaFree(L->d_tab);
+    if (L->h_tab) cudaFreeHost(L->h_tab);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     delete L;
     return st;

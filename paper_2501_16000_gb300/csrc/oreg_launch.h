@@ -50,6 +50,7 @@ struct ModeSpec {
     int active;
     int m, n;
     double ex, ey;
+    const double *tab;  // [sin(2 pi m x/nx) | cos(..) over x, sin(2 pi n y/ny) | cos(..) over y]
 };
 
 #define OREG_DECLARE_LAUNCHERS(SUFFIX)                                                            \

@@ -20,7 +20,7 @@
 #include <mutex>
 
 #include "oreg.h"
-#include "oreg_kernels.cuh"
+#include "oreg_aux.cuh"
 
 namespace oreg {
 void set_last_error_message(const char *msg);

@@ -1,4 +1,5 @@
 // Kernel instantiations for bf16 population storage.
+#include "oreg_aux.cuh"
 #include "oreg_kernels.cuh"
 
 OREG_DEFINE_LAUNCHERS(bf16, oreg::ST_BF16)

@@ -1,4 +1,5 @@
 // Kernel instantiations for f16 population storage.
+#include "oreg_aux.cuh"
 #include "oreg_kernels.cuh"
 
 OREG_DEFINE_LAUNCHERS(f16, oreg::ST_F16)

@@ -52,6 +52,7 @@ class Lattice:
         self.eq, self.coll, self.storage, self.layout = eq, coll, storage, layout
         self._buf = None
         self._handle = None
+        self.stream = None  # torch stream the lattice runs on (torch memory only)
         kw = dict(nx=nx, ny=ny, tau=tau, theta=theta, eq=eq, coll=coll, storage=storage,
                   layout=layout, rho0=rho0)
         dev_ptr, nbytes, sptr = 0, 0, 0
@@ -72,7 +73,12 @@ class Lattice:
             self._buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
             dev_ptr = self._buf.data_ptr()
             s = stream if stream is not None else torch.cuda.current_stream()
-            self._torch_stream = s
+            if s.cuda_stream == 0:
+                # torch's legacy default stream has handle 0, which the C ABI
+                # reads as "create a stream": give the lattice a torch stream
+                # of its own instead, so callers can order work against it
+                s = torch.cuda.Stream()
+            self.stream = s
             sptr = s.cuda_stream
         self.params = make_params(**kw, device_buffer=dev_ptr, buffer_bytes=nbytes, stream=sptr)
         h = ctypes.c_void_p()

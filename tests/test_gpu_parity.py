@@ -40,10 +40,13 @@ def oracle_run(case, steps):
     return O.run(f0, p, steps)
 
 
-def gpu_run(case, steps, storage, layout, split=None):
+def gpu_run(case, steps, storage, layout, split=None, comp=None):
+    from paper_2501_16000_gb300 import binding as B
     from paper_2501_16000_gb300.engine import Lattice
     with Lattice(case.nx, case.ny, case.tau, case.theta, case.eq, case.coll, storage,
                  layout) as lat:
+        if comp is not None:
+            lat.set_option(B.OLB_OPT_COMPENSATED, comp)
         lat.init_case(case)
         if split:
             for k in split:
@@ -92,14 +95,16 @@ def test_config1_shear_wave_fp32(case):
 TOL_F32_SHOCK_2000 = 5e-5
 
 
+@pytest.mark.parametrize("comp", [0, 1])
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 @pytest.mark.parametrize("case", CONFIG2, ids=lambda c: f"shock-{c.eq}")
-def test_config2_shock_tube_fp32(case, layout):
-    err = rel_linf(gpu_run(case, case.steps, "f32", layout), oracle_run(case, case.steps))
-    print(f"FP32 shock {case.eq} {layout} t=2000: rel Linf {err:.3e}")
+def test_config2_shock_tube_fp32(case, layout, comp):
+    opts = {"comp": comp}
+    err = rel_linf(gpu_run(case, case.steps, "f32", layout, **opts), oracle_run(case, case.steps))
+    print(f"FP32 shock {case.eq} {layout} comp={comp} t=2000: rel Linf {err:.3e}")
     assert err <= TOL_F32_SHOCK_2000, err
-    err500 = rel_linf(gpu_run(case, 500, "f32", layout), oracle_run(case, 500))
-    print(f"FP32 shock {case.eq} {layout} t=500: rel Linf {err500:.3e}")
+    err500 = rel_linf(gpu_run(case, 500, "f32", layout, **opts), oracle_run(case, 500))
+    print(f"FP32 shock {case.eq} {layout} comp={comp} t=500: rel Linf {err500:.3e}")
     assert err500 <= TOL["f32"], err500
 
 
