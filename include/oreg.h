@@ -180,6 +180,65 @@ olb_status olb_diagnostics(olb_lattice *lat, double *mass, double *mom_x, double
  * the decay statistic of Sec. IV.  Synchronises the stream. */
 olb_status olb_wave_amplitude(olb_lattice *lat, int32_t m, int32_t n, double *amp);
 
+/* ------------------------------------------------------------------------
+ * Batched path: many independent lattices advanced together.
+ *
+ * One persistent kernel per time step walks a flattened table of warp work
+ * items (one row segment of one member lattice each); steps_per_launch such
+ * launches are captured once in a CUDA graph and replayed per round.  Each
+ * member keeps its own size, relaxation time, temperature, equilibrium and
+ * collision; all members share the batch's storage format and layout and
+ * must have been created on the batch's stream.  Joining and leaving rewrite
+ * the device tables only (the graph is captured once).  A member is advanced
+ * exactly the number of steps it was added with, then idles until removed.
+ * Results are bitwise those of olb_step on the same lattice: each node's
+ * update depends only on that lattice's state.
+ * ---------------------------------------------------------------------- */
+typedef struct olb_batch olb_batch; /* opaque; owned by the library */
+
+typedef struct {
+    int32_t storage;           /* olb_storage of every member */
+    int32_t layout;            /* olb_layout of every member */
+    int32_t max_lattices;      /* descriptor capacity */
+    int64_t max_items;         /* work-item capacity: sum over members of
+                                  ny * ceil(nx / (32 * 16 / element size)) */
+    int32_t steps_per_launch;  /* K: time steps per graph replay (1..10000) */
+    int32_t warps_per_block;   /* 1, 2, 4 or 8 */
+    int32_t blocks_per_sm;     /* persistent grid = blocks_per_sm x SMs;
+                                  0 = the kernel's occupancy limit */
+    void *cuda_stream;         /* stream of the batch and of every member;
+                                  NULL: the library creates and owns one */
+} olb_batch_params;
+
+olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out);
+
+/* Adds an initialised lattice that will advance nsteps more steps over the
+ * following rounds.  Waits for the batch's pending rounds.  While a member,
+ * the lattice is advanced only by olb_batch_run (olb_step and the init calls
+ * return OLB_ERR_STATE); its readback calls may be used between rounds. */
+olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps);
+
+/* Removes a member (waits for the batch's pending rounds). olb_destroy of a
+ * member removes it first. */
+olb_status olb_batch_remove(olb_batch *b, olb_lattice *lat);
+
+/* Enqueues nrounds graph replays of steps_per_launch steps each
+ * (asynchronous on the batch's stream); member times advance accordingly. */
+olb_status olb_batch_run(olb_batch *b, int64_t nrounds);
+
+/* Waits until the batch's enqueued rounds have finished. */
+olb_status olb_batch_wait(olb_batch *b);
+
+/* Steps a member still has to take. */
+olb_status olb_batch_remaining(const olb_batch *b, const olb_lattice *lat, int64_t *steps);
+
+/* Number of members / of work items in the batch's tables. */
+int32_t olb_batch_size(const olb_batch *b);
+int64_t olb_batch_work_items(const olb_batch *b);
+
+/* Releases the batch (waits first); members stay valid lattices. */
+olb_status olb_batch_destroy(olb_batch *b);
+
 /* Largest ny olb_diagnostics_noalloc accepts. */
 #define OLB_NOALLOC_MAX_ROWS 16384
 

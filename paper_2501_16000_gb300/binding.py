@@ -46,6 +46,13 @@ class olb_params(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p)]
 
 
+class olb_batch_params(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("max_lattices", ctypes.c_int32), ("max_items", ctypes.c_int64),
+                ("steps_per_launch", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
 _P = ctypes.POINTER
 _d = _P(ctypes.c_double)
 _h = ctypes.c_void_p
@@ -75,6 +82,15 @@ SIGNATURES = {
     "olb_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, _P(olb_params), ctypes.c_int64,
                                                ctypes.c_void_p]),
     "olb_destroy": (ctypes.c_int, [_h]),
+    "olb_batch_create": (ctypes.c_int, [_P(olb_batch_params), _P(_h)]),
+    "olb_batch_add": (ctypes.c_int, [_h, _h, ctypes.c_int64]),
+    "olb_batch_remove": (ctypes.c_int, [_h, _h]),
+    "olb_batch_run": (ctypes.c_int, [_h, ctypes.c_int64]),
+    "olb_batch_wait": (ctypes.c_int, [_h]),
+    "olb_batch_remaining": (ctypes.c_int, [_h, _h, _P(ctypes.c_int64)]),
+    "olb_batch_size": (ctypes.c_int32, [_h]),
+    "olb_batch_work_items": (ctypes.c_int64, [_h]),
+    "olb_batch_destroy": (ctypes.c_int, [_h]),
     "olb_last_error": (ctypes.c_char_p, []),
 }
 

@@ -12,6 +12,7 @@
 #include "oreg.h"
 #include "oreg_device.cuh"
 #include "oreg_launch.h"
+#include "oreg_lattice.h"
 
 using namespace oreg;
 
@@ -63,33 +64,6 @@ namespace oreg {
 void set_last_error_message(const char *msg) { g_last_error = msg; }
 }  // namespace oreg
 
-struct olb_lattice {
-    olb_params p;
-    int V;
-    size_t esize;
-    int pitch;
-    size_t plane;         // elements per plane
-    size_t buf_elems;     // elements per population buffer (9 planes)
-    int nbuf;
-    void *mem;            // population memory (2 buffers for A-B, 1 for AA)
-    bool own_mem;
-    cudaStream_t stream;
-    bool own_stream;
-    int64_t t;            // time of the canonical state; -1 = uninitialised
-    int comp;
-    int warps_per_block;
-    int num_sms;
-    double *d_red;        // reduction partials + result (library scratch)
-    double *h_red;        // pinned host copy of the result
-    int red_blocks;
-    void *d_chunk;        // readback scratch (lazy)
-    size_t chunk_bytes;
-    double *d_tab;        // shear-mode sin/cos tables (lazy), for (tab_m, tab_n)
-    double *h_tab;
-    int tab_m, tab_n;
-    CollConst<double> kd;     // FP64 constants (shift as stored type's shift)
-    CollConst<float> kf;      // FP32 constants (F32, F16, BF16 compute)
-};
 
 namespace {
 
@@ -206,6 +180,8 @@ void *state_base(const olb_lattice *L) {
 
 olb_status check_lattice(const olb_lattice *L, bool need_state) {
     if (!L) return fail(OLB_ERR_INVALID, "lattice is NULL");
+    if (L->batch && !need_state)
+        return fail(OLB_ERR_STATE, "lattice belongs to a batch: remove it before re-initialising");
     if (need_state && L->t < 0) return fail(OLB_ERR_STATE, "lattice state not initialised (call an olb_init_* first)");
     return OLB_OK;
 }
@@ -468,6 +444,7 @@ olb_status olb_init_fields(olb_lattice *L, const double *rho, const double *ux, 
 olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     olb_status st = check_lattice(L, true);
     if (st != OLB_OK) return st;
+    if (L->batch) return fail(OLB_ERR_STATE, "lattice belongs to a batch: it advances with olb_batch_run");
     if (nsteps < 0) return fail(OLB_ERR_INVALID, "nsteps must be >= 0");
     StepArgs a{};
     a.nx = L->p.nx;
@@ -670,6 +647,7 @@ olb_status olb_wave_amplitude(olb_lattice *L, int32_t m, int32_t n, double *amp)
 olb_status olb_destroy(olb_lattice *L) {
     if (!L) return OLB_OK;
     olb_status st = OLB_OK;
+    if (L->batch) st = olb_batch_remove(L->batch, L);
     if (L->stream) {
         cudaError_t e = cudaStreamSynchronize(L->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "synchronising before destroy");

@@ -1,0 +1,336 @@
+// C ABI of the batched path (olb_batch_*): many independent lattices advanced
+// together by one persistent kernel per time step, K steps per CUDA-graph
+// replay.  See oreg_batch_kernels.cuh for the device side.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "oreg.h"
+#include "oreg_batch_kernels.cuh"
+#include "oreg_launch.h"
+#include "oreg_lattice.h"
+
+using namespace oreg;
+
+namespace {
+
+olb_status bfail(olb_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_last_error_message(buf);
+    return st;
+}
+
+olb_status bcuda(cudaError_t e, const char *what) {
+    return bfail(e == cudaErrorMemoryAllocation ? OLB_ERR_NOMEM : OLB_ERR_CUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+#define B_CUDA(call, what)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return bcuda(e_, what);      \
+    } while (0)
+
+#define BDISPATCH(storage, fn, ...)                                     \
+    ((storage) == OLB_F64   ? fn##_f64(__VA_ARGS__)                     \
+     : (storage) == OLB_F32 ? fn##_f32(__VA_ARGS__)                     \
+     : (storage) == OLB_F16_SHIFTED ? fn##_f16(__VA_ARGS__)             \
+                                    : fn##_bf16(__VA_ARGS__))
+
+struct Member {
+    olb_lattice *lat;
+    long long g_base, g_end;  // active global steps [g_base, g_end)
+    long long t_base;         // lattice time at g_base
+};
+
+template <typename C>
+void fill_desc(void *dst, const Member &m, const CollConst<C> &k) {
+    BatchDesc<C> d;
+    std::memset(&d, 0, sizeof d);
+    const olb_lattice *L = m.lat;
+    d.mem = L->mem;
+    d.nx = L->p.nx;
+    d.ny = L->p.ny;
+    d.pitch = L->pitch;
+    d.eq = L->p.eq;
+    d.coll = L->p.coll;
+    d.plane = L->plane;
+    d.buf_elems = L->buf_elems;
+    d.t_base = m.t_base;
+    d.g_base = m.g_base;
+    d.g_end = m.g_end;
+    d.k = k;
+    std::memcpy(dst, &d, sizeof d);
+}
+
+}  // namespace
+
+struct olb_batch {
+    olb_batch_params p;
+    cudaStream_t stream;
+    bool own_stream;
+    int num_sms;
+    int grid, block;
+    size_t desc_size;
+    // device tables
+    char *d_descs;
+    int4 *d_items;
+    int *d_nitems;
+    long long *d_g;
+    // host mirrors
+    std::vector<Member> members;
+    std::vector<char> h_descs;
+    std::vector<int4> h_items;
+    int *h_nitems;          // pinned
+    long long G;            // global step counter at the start of the next round
+    bool captured;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+olb_status upload(olb_batch *b) {
+    const size_t nm = b->members.size();
+    b->h_descs.assign(nm * b->desc_size, 0);
+    b->h_items.clear();
+    for (size_t j = 0; j < nm; ++j) {
+        const Member &m = b->members[j];
+        const olb_lattice *L = m.lat;
+        if (L->p.storage == OLB_F64) fill_desc<double>(&b->h_descs[j * b->desc_size], m, L->kd);
+        else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf);
+        const int segs = (L->p.nx + 32 * L->V - 1) / (32 * L->V);
+        for (int y = 0; y < L->p.ny; ++y)
+            for (int s = 0; s < segs; ++s) b->h_items.push_back(make_int4((int)j, y, s, 0));
+    }
+    if ((long long)b->h_items.size() > b->p.max_items)
+        return bfail(OLB_ERR_NOMEM, "batch work items %zu exceed max_items %lld", b->h_items.size(),
+                     (long long)b->p.max_items);
+    *b->h_nitems = (int)b->h_items.size();
+    if (nm)
+        B_CUDA(cudaMemcpyAsync(b->d_descs, b->h_descs.data(), b->h_descs.size(),
+                               cudaMemcpyHostToDevice, b->stream),
+               "uploading batch descriptors");
+    if (!b->h_items.empty())
+        B_CUDA(cudaMemcpyAsync(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(int4),
+                               cudaMemcpyHostToDevice, b->stream),
+               "uploading batch items");
+    B_CUDA(cudaMemcpyAsync(b->d_nitems, b->h_nitems, sizeof(int), cudaMemcpyHostToDevice,
+                           b->stream),
+           "uploading item count");
+    // the host vectors may change on the next call
+    B_CUDA(cudaStreamSynchronize(b->stream), "synchronising batch upload");
+    return OLB_OK;
+}
+
+__global__ void k_batch_advance(long long *g, int K) { *g += K; }
+
+olb_status capture(olb_batch *b) {
+    BatchLaunch a{};
+    a.descs = b->d_descs;
+    a.items = b->d_items;
+    a.n_items = b->d_nitems;
+    a.g = b->d_g;
+    a.layout = b->p.layout;
+    a.grid = b->grid;
+    a.block = b->block;
+    a.stream = b->stream;
+    B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
+           "beginning graph capture");
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < b->p.steps_per_launch && e == cudaSuccess; ++k) {
+        a.k = k;
+        e = BDISPATCH(b->p.storage, batch_step, a);
+    }
+    if (e == cudaSuccess) {
+        k_batch_advance<<<1, 1, 0, b->stream>>>(b->d_g, b->p.steps_per_launch);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bcuda(e, "capturing batch steps");
+    }
+    if (e2 != cudaSuccess) return bcuda(e2, "ending graph capture");
+    b->graph = g;
+    B_CUDA(cudaGraphInstantiate(&b->exec, g, 0), "instantiating batch graph");
+    b->captured = true;
+    return OLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out) {
+    if (!out) return bfail(OLB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!p) return bfail(OLB_ERR_INVALID, "params is NULL");
+    if (p->storage < OLB_F64 || p->storage > OLB_BF16_SHIFTED)
+        return bfail(OLB_ERR_INVALID, "unknown storage %d", p->storage);
+    if (p->layout != OLB_LAYOUT_AB && p->layout != OLB_LAYOUT_AA)
+        return bfail(OLB_ERR_INVALID, "unknown layout %d", p->layout);
+    if (p->max_lattices < 1 || p->max_items < 1)
+        return bfail(OLB_ERR_INVALID, "max_lattices and max_items must be >= 1");
+    if (p->steps_per_launch < 1 || p->steps_per_launch > 10000)
+        return bfail(OLB_ERR_INVALID, "steps_per_launch must be in [1, 10000]");
+    if (p->warps_per_block < 1 || p->warps_per_block > 8 ||
+        (p->warps_per_block & (p->warps_per_block - 1)))
+        return bfail(OLB_ERR_INVALID, "warps_per_block must be 1, 2, 4 or 8");
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32)
+        return bfail(OLB_ERR_INVALID, "blocks_per_sm must be in [0, 32] (0 = occupancy limit)");
+    olb_batch *b = new (std::nothrow) olb_batch();
+    if (!b) return bfail(OLB_ERR_NOMEM, "host allocation of the batch failed");
+    b->p = *p;
+    b->desc_size = BDISPATCH(p->storage, batch_desc_size);
+    auto bail = [&](olb_status s) {
+        olb_batch_destroy(b);
+        return s;
+    };
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return bail(bcuda(e, "querying the device"));
+    if (p->cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(p->cuda_stream);
+        b->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(bcuda(e, "creating the stream"));
+        b->own_stream = true;
+    }
+    b->block = 32 * p->warps_per_block;
+    int per_sm = p->blocks_per_sm;
+    if (per_sm == 0) {
+        per_sm = BDISPATCH(p->storage, batch_occupancy, p->layout, b->block);
+        if (per_sm < 1) per_sm = 1;
+    }
+    b->grid = per_sm * b->num_sms;
+    e = cudaMalloc(&b->d_descs, (size_t)p->max_lattices * b->desc_size);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, (size_t)p->max_items * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_nitems, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_g, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_nitems, sizeof(int));
+    if (e != cudaSuccess) return bail(bcuda(e, "allocating batch tables"));
+    *b->h_nitems = 0;
+    e = cudaMemsetAsync(b->d_g, 0, sizeof(long long), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nitems, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bail(bcuda(e, "clearing batch tables"));
+    b->G = 0;
+    *out = b;
+    return OLB_OK;
+}
+
+olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps) {
+    if (!b || !lat) return bfail(OLB_ERR_INVALID, "batch and lattice must not be NULL");
+    if (nsteps < 0) return bfail(OLB_ERR_INVALID, "nsteps must be >= 0");
+    if (lat->batch) return bfail(OLB_ERR_STATE, "lattice already belongs to a batch");
+    if (lat->t < 0) return bfail(OLB_ERR_STATE, "lattice state not initialised");
+    if (lat->p.storage != b->p.storage || lat->p.layout != b->p.layout)
+        return bfail(OLB_ERR_INVALID, "lattice storage/layout (%d/%d) differ from the batch's (%d/%d)",
+                     lat->p.storage, lat->p.layout, b->p.storage, b->p.layout);
+    if (lat->stream != b->stream)
+        return bfail(OLB_ERR_INVALID, "member lattices must be created on the batch's stream");
+    if ((int)b->members.size() >= b->p.max_lattices)
+        return bfail(OLB_ERR_NOMEM, "batch holds max_lattices = %d lattices", b->p.max_lattices);
+    B_CUDA(cudaStreamSynchronize(b->stream), "waiting for the batch");
+    Member m;
+    m.lat = lat;
+    m.g_base = b->G;
+    m.g_end = b->G + nsteps;
+    m.t_base = lat->t;
+    b->members.push_back(m);
+    olb_status st = upload(b);
+    if (st != OLB_OK) {
+        b->members.pop_back();
+        upload(b);
+        return st;
+    }
+    lat->batch = b;
+    return OLB_OK;
+}
+
+olb_status olb_batch_remove(olb_batch *b, olb_lattice *lat) {
+    if (!b || !lat) return bfail(OLB_ERR_INVALID, "batch and lattice must not be NULL");
+    auto it = std::find_if(b->members.begin(), b->members.end(),
+                           [&](const Member &m) { return m.lat == lat; });
+    if (it == b->members.end()) return bfail(OLB_ERR_INVALID, "lattice is not in this batch");
+    B_CUDA(cudaStreamSynchronize(b->stream), "waiting for the batch");
+    b->members.erase(it);
+    lat->batch = nullptr;
+    return upload(b);
+}
+
+olb_status olb_batch_run(olb_batch *b, int64_t nrounds) {
+    if (!b) return bfail(OLB_ERR_INVALID, "batch is NULL");
+    if (nrounds < 0) return bfail(OLB_ERR_INVALID, "nrounds must be >= 0");
+    if (!b->captured) {
+        olb_status st = capture(b);
+        if (st != OLB_OK) return st;
+    }
+    const long long K = b->p.steps_per_launch;
+    for (int64_t r = 0; r < nrounds; ++r) {
+        B_CUDA(cudaGraphLaunch(b->exec, b->stream), "launching batch graph");
+        // member times advance by the steps each takes part in this round
+        for (Member &m : b->members) {
+            const long long lo = std::max(m.g_base, b->G), hi = std::min(m.g_end, b->G + K);
+            if (hi > lo) m.lat->t += hi - lo;
+        }
+        b->G += K;
+    }
+    return OLB_OK;
+}
+
+olb_status olb_batch_wait(olb_batch *b) {
+    if (!b) return bfail(OLB_ERR_INVALID, "batch is NULL");
+    B_CUDA(cudaStreamSynchronize(b->stream), "waiting for the batch");
+    return OLB_OK;
+}
+
+olb_status olb_batch_remaining(const olb_batch *b, const olb_lattice *lat, int64_t *steps) {
+    if (!b || !lat || !steps) return bfail(OLB_ERR_INVALID, "NULL argument");
+    for (const Member &m : b->members)
+        if (m.lat == lat) {
+            *steps = std::max<long long>(0, m.g_end - std::max(m.g_base, b->G));
+            return OLB_OK;
+        }
+    return bfail(OLB_ERR_INVALID, "lattice is not in this batch");
+}
+
+int32_t olb_batch_size(const olb_batch *b) { return b ? (int32_t)b->members.size() : 0; }
+
+int64_t olb_batch_work_items(const olb_batch *b) { return b ? (int64_t)b->h_items.size() : 0; }
+
+olb_status olb_batch_destroy(olb_batch *b) {
+    if (!b) return OLB_OK;
+    olb_status st = OLB_OK;
+    if (b->stream) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) st = bcuda(e, "synchronising before destroy");
+    }
+    for (Member &m : b->members) m.lat->batch = nullptr;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->d_descs) cudaFree(b->d_descs);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_nitems) cudaFree(b->d_nitems);
+    if (b->d_g) cudaFree(b->d_g);
+    if (b->h_nitems) cudaFreeHost(b->h_nitems);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return st;
+}
+
+}  // extern "C"

@@ -56,18 +56,15 @@ __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<
     }
 }
 
+// One warp work item: row y, segment seg (32*V nodes) of a lattice.
 template <int S, int EQ, int COLL, bool COMP>
-__global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *__restrict__ src,
-                                                 typename Storage<S>::T *__restrict__ dst, int nx,
-                                                 int ny, int pitch, size_t plane, int segs,
-                                                 const CollConst<typename Storage<S>::C> k) {
+__device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict__ src,
+                                        typename Storage<S>::T *__restrict__ dst, int nx, int ny,
+                                        int pitch, size_t plane, int y, int seg, int lane,
+                                        const CollConst<typename Storage<S>::C> &k) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int lane = threadIdx.x & 31;
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (item >= (long long)ny * segs) return;  // warp-uniform
-    const int y = (int)(item / segs), seg = (int)(item % segs);
     const int xb = seg * 32 * V + lane * V;
 
     C f[9][V];
@@ -96,6 +93,17 @@ __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *_
     }
 }
 
+template <int S, int EQ, int COLL, bool COMP>
+__global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *__restrict__ src,
+                                                 typename Storage<S>::T *__restrict__ dst, int nx,
+                                                 int ny, int pitch, size_t plane, int segs,
+                                                 const CollConst<typename Storage<S>::C> k) {
+    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= (long long)ny * segs) return;  // warp-uniform
+    item_ab<S, EQ, COLL, COMP>(src, dst, nx, ny, pitch, plane, (int)(item / segs),
+                               (int)(item % segs), threadIdx.x & 31, k);
+}
+
 // ---------------------------------------------------------------------------
 // Stream-collide, in-place AA layout.
 //   even step: read the node's own slots i, write post_i into slot opp(i);
@@ -104,18 +112,14 @@ __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *_
 // only, so the update is race-free in place.
 // ---------------------------------------------------------------------------
 template <int S, int EQ, int COLL, bool COMP>
-__global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A, int nx, int ny,
-                                                      int pitch, size_t plane, int segs,
-                                                      const CollConst<typename Storage<S>::C> k) {
+__device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, int pitch,
+                                             size_t plane, int y, int seg, int lane,
+                                             const CollConst<typename Storage<S>::C> &k) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int lane = threadIdx.x & 31;
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (item >= (long long)ny * segs) return;
-    const int y = (int)(item / segs), seg = (int)(item % segs);
     const int xb = seg * 32 * V + lane * V;
-    if (xb >= nx) return;  // no shuffles in this kernel
+    if (xb >= nx) return;  // no shuffles in the even step
     typename ST::T *row = A + (size_t)y * pitch + xb;
     C f[9][V];
 #pragma unroll
@@ -135,6 +139,16 @@ __global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A,
     }
 }
 
+template <int S, int EQ, int COLL, bool COMP>
+__global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A, int nx, int ny,
+                                                      int pitch, size_t plane, int segs,
+                                                      const CollConst<typename Storage<S>::C> k) {
+    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= (long long)ny * segs) return;
+    item_aa_even<S, EQ, COLL, COMP>(A, nx, pitch, plane, (int)(item / segs), (int)(item % segs),
+                                    threadIdx.x & 31, k);
+}
+
 template <int S, int I>
 __device__ __forceinline__ void push_plane(typename Storage<S>::T *A, size_t plane, int pitch,
                                            int y, int ny, int xb, int nx, int lane,
@@ -144,16 +158,12 @@ __device__ __forceinline__ void push_plane(typename Storage<S>::T *A, size_t pla
 }
 
 template <int S, int EQ, int COLL, bool COMP>
-__global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
-                                                     int pitch, size_t plane, int segs,
-                                                     const CollConst<typename Storage<S>::C> k) {
+__device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, int ny, int pitch,
+                                            size_t plane, int y, int seg, int lane,
+                                            const CollConst<typename Storage<S>::C> &k) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int lane = threadIdx.x & 31;
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (item >= (long long)ny * segs) return;
-    const int y = (int)(item / segs), seg = (int)(item % segs);
     const int xb = seg * 32 * V + lane * V;
 
     C f[9][V];
@@ -179,6 +189,16 @@ __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, 
     push_plane<S, 6>(A, plane, pitch, y, ny, xb, nx, lane, f[6]);
     push_plane<S, 7>(A, plane, pitch, y, ny, xb, nx, lane, f[7]);
     push_plane<S, 8>(A, plane, pitch, y, ny, xb, nx, lane, f[8]);
+}
+
+template <int S, int EQ, int COLL, bool COMP>
+__global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
+                                                     int pitch, size_t plane, int segs,
+                                                     const CollConst<typename Storage<S>::C> k) {
+    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= (long long)ny * segs) return;
+    item_aa_odd<S, EQ, COLL, COMP>(A, nx, ny, pitch, plane, (int)(item / segs), (int)(item % segs),
+                                   threadIdx.x & 31, k);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,46 @@
+// Internal definition of the opaque olb_lattice handle (shared by the C-ABI
+// translation units; not part of the public header).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "oreg.h"
+#include "oreg_device.cuh"
+
+struct olb_batch;
+
+struct olb_lattice {
+    olb_params p;
+    int V;
+    size_t esize;
+    int pitch;
+    size_t plane;         // elements per plane
+    size_t buf_elems;     // elements per population buffer (9 planes)
+    int nbuf;
+    void *mem;            // population memory (2 buffers for A-B, 1 for AA)
+    bool own_mem;
+    cudaStream_t stream;
+    bool own_stream;
+    int64_t t;            // time of the canonical state; -1 = uninitialised
+    int comp;
+    int warps_per_block;
+    int num_sms;
+    double *d_red;        // reduction partials + result (library scratch)
+    double *h_red;        // pinned host copy of the result
+    int red_blocks;
+    void *d_chunk;        // readback scratch (lazy)
+    size_t chunk_bytes;
+    double *d_tab;        // shear-mode sin/cos tables (lazy), for (tab_m, tab_n)
+    double *h_tab;
+    int tab_m, tab_n;
+    oreg::CollConst<double> kd;     // FP64 constants (shift as stored type's shift)
+    oreg::CollConst<float> kf;      // FP32 constants (F32, F16, BF16 compute)
+    olb_batch *batch;               // batch the lattice currently belongs to, or NULL
+};
+
+namespace oreg {
+// Records the message of a failed call for olb_last_error() (oreg_api.cu).
+void set_last_error_message(const char *msg);
+}  // namespace oreg

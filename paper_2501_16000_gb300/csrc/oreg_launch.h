@@ -75,6 +75,28 @@ OREG_DECLARE_LAUNCHERS(f32)
 OREG_DECLARE_LAUNCHERS(f16)
 OREG_DECLARE_LAUNCHERS(bf16)
 
+// One launch of the batched stream-collide kernel (see oreg_batch_kernels.cuh).
+struct BatchLaunch {
+    const void *descs;        // BatchDesc<C>[]
+    const int4 *items;        // work items (descriptor, row, segment)
+    const int *n_items;       // device: number of valid items
+    const long long *g;       // device: global step counter of this round
+    int k;                    // step within the round
+    int layout;
+    int grid, block;
+    cudaStream_t stream;
+};
+
+#define OREG_DECLARE_BATCH_LAUNCHERS(SUFFIX)                 \
+    cudaError_t batch_step_##SUFFIX(const BatchLaunch &a);   \
+    int batch_occupancy_##SUFFIX(int layout, int block);     \
+    size_t batch_desc_size_##SUFFIX();
+
+OREG_DECLARE_BATCH_LAUNCHERS(f64)
+OREG_DECLARE_BATCH_LAUNCHERS(f32)
+OREG_DECLARE_BATCH_LAUNCHERS(f16)
+OREG_DECLARE_BATCH_LAUNCHERS(bf16)
+
 constexpr int RED_BLOCKS_MAX = 1216;  // fixed reduction grid (8 x 152 SMs)
 constexpr int RED_QUANTITIES = 5;
 

@@ -1,0 +1,112 @@
+"""Batched path on the GPU: every lattice advanced in a mixed batch (uneven
+sizes, own tau/theta/equilibrium/collision, joining at different rounds,
+finishing at different steps) ends bitwise equal to the same lattice advanced
+alone with olb_step; and the FP64 batch matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_16000_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_16000_gb300 import build
+    build.build()
+
+
+def mixed_cases():
+    cases = W.batch_mix(count=12, seed=7, lo=5, hi=300, steps=0)
+    extra = [W.LatticeCase(nx=37, ny=3, tau=0.7, theta=0.35, coll="bgk", case="shear", u0=0.03,
+                           m=1, n=1),
+             W.LatticeCase(nx=130, ny=9, tau=0.55, eq="poly2", case="shock", x_split=40),
+             W.LatticeCase(nx=1, ny=7, tau=0.9, case="shear", m=0, n=1, u0=0.02)]
+    return cases + extra
+
+
+@pytest.mark.parametrize("storage", ["f16", "f32", "bf16"])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_batch_equals_alone_bitwise(storage, layout):
+    from paper_2501_16000_gb300.batch import BatchEngine
+    from paper_2501_16000_gb300.engine import Lattice
+    cases = mixed_cases()
+    K = 7
+    steps = [5 + 3 * j for j in range(len(cases))]        # odd and even totals, mid-round ends
+    with BatchEngine(storage, layout, max_lattices=64, max_items=1 << 16, steps_per_launch=K,
+                     warps_per_block=4) as eng:
+        lats = []
+        for j, c in enumerate(cases):
+            lat = eng.new_lattice(c)
+            lats.append(lat)
+            if j % 3 != 2:
+                eng.add(lat, steps[j])
+        eng.run(1)                                       # some join one round late
+        for j, lat in enumerate(lats):
+            if j % 3 == 2:
+                eng.add(lat, steps[j])
+        rounds = max(steps) // K + 2
+        eng.run(rounds)
+        eng.wait()
+        for j, lat in enumerate(lats):
+            assert lat.time == steps[j]
+            assert eng.remaining(lat) == 0
+        got = [lat.populations() for lat in lats]
+        for lat in lats:
+            lat.close()
+    for j, c in enumerate(cases):
+        with Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, storage, layout) as ref:
+            ref.init_case(c)
+            ref.step(steps[j])
+            assert np.array_equal(ref.populations(), got[j]), (j, c)
+
+
+def test_batch_fp64_matches_oracle():
+    from paper_2501_16000_gb300.batch import BatchEngine
+    cases = mixed_cases()[:6]
+    with BatchEngine("f64", "aa", max_lattices=16, max_items=1 << 14, steps_per_launch=10) as eng:
+        lats = [eng.new_lattice(c) for c in cases]
+        for lat in lats:
+            eng.add(lat, 23)
+        eng.run(3)
+        eng.wait()
+        for lat, c in zip(lats, cases):
+            p = O.params(c.nx, c.ny, c.tau, c.theta, O.GUIDED if c.eq == "guided" else O.POLY2,
+                         O.OREG if c.coll == "oreg" else O.BGK)
+            ref = O.run(O.init_equilibrium(p, *c.fields()), p, 23)
+            err = np.abs(lat.populations() - ref).max() / np.abs(ref).max()
+            assert err <= 1e-12, (c, err)
+            lat.close()
+
+
+def test_batch_membership_rules():
+    from paper_2501_16000_gb300 import binding as B
+    from paper_2501_16000_gb300.batch import BatchEngine
+    from paper_2501_16000_gb300.engine import Lattice
+    with BatchEngine("f16", "ab", max_lattices=2, max_items=64, steps_per_launch=4) as eng:
+        c = W.LatticeCase(nx=64, ny=8, tau=0.8, case="shear", m=1, n=1)
+        a = eng.new_lattice(c)
+        eng.add(a, 8)
+        with pytest.raises(B.OregError) as e:      # members advance only with the batch
+            a.step(1)
+        assert e.value.status == B.OLB_ERR_STATE
+        with pytest.raises(B.OregError) as e:      # same storage/layout required
+            other = Lattice(64, 8, 0.8, storage="f32", layout="ab", stream=eng.stream)
+            eng.add(other, 1)
+        other.close()
+        big = eng.new_lattice(W.LatticeCase(nx=256, ny=100, tau=0.8, case="shock", x_split=10))
+        with pytest.raises(B.OregError) as e:      # work-item capacity
+            eng.add(big, 1)
+        assert e.value.status == B.OLB_ERR_NOMEM
+        big.close()
+        eng.run(3)
+        eng.wait()
+        assert a.time == 8
+        eng.remove(a)
+        a.step(1)                                  # free again after removal
+        assert a.time == 9
+        a.close()
