@@ -55,7 +55,9 @@ typedef enum { OLB_COLL_OREG = 0, OLB_COLL_BGK = 1 } olb_collision;
 /* Population storage.  Every format stores shifted values g_i = f_i - s_i,
  * with s_i the rest equilibrium w_i(theta) rho0 rounded to the compute type
  * (w = (1-theta)^2, theta(1-theta)/2, theta^2/4 for rest, axis and diagonal
- * directions).  F64 computes in double; F32, F16 and BF16 compute in float. */
+ * directions).  F64 computes in double; F32, F16 and BF16 compute in float.
+ * F16 stores g * 2^8 (exact scaling) to keep small deviations out of the f16
+ * subnormal range; |f_i - s_i| must stay below 255. */
 typedef enum {
     OLB_F64 = 0,
     OLB_F32 = 1,
@@ -99,7 +101,15 @@ typedef enum {
     /* warps per thread block of the stream-collide kernels: 1, 2, 4 or 8
        (default 4).  Each warp updates 32*V consecutive nodes of one row,
        V = 16 bytes / element size. */
-    OLB_OPT_WARPS_PER_BLOCK = 2
+    OLB_OPT_WARPS_PER_BLOCK = 2,
+    /* 1 (default for OLB_F16_SHIFTED and OLB_BF16_SHIFTED): round the
+       post-collision values to the half format stochastically, with random
+       bits drawn from a counter-based hash of (x, y, t, direction), so that
+       rounding adds no bias to slow, small-amplitude dynamics (round-to-
+       nearest there changes a shear wave's decay rate by up to ~1e-1 at
+       tau = 0.52); results stay deterministic and independent of batching
+       and layout.  0: round to nearest even.  Ignored by F32 and F64. */
+    OLB_OPT_STOCHASTIC_ROUNDING = 3
 } olb_option;
 
 /* Version of this ABI (bumped on incompatible change). */

@@ -308,6 +308,7 @@ olb_status olb_create_lattice(const olb_params *p, olb_lattice **out) {
     L->nbuf = p->layout == OLB_LAYOUT_AB ? 2 : 1;
     L->t = -1;
     L->comp = 0;
+    L->sr = (p->storage == OLB_F16_SHIFTED || p->storage == OLB_BF16_SHIFTED) ? 1 : 0;
     L->warps_per_block = 4;
     L->kd = make_const_f64_for(p);
     L->kf = make_const<float>(p);
@@ -367,6 +368,10 @@ olb_status olb_set_option(olb_lattice *L, int32_t option, int64_t value) {
         case OLB_OPT_COMPENSATED:
             if (value != 0 && value != 1) return fail(OLB_ERR_INVALID, "OLB_OPT_COMPENSATED takes 0 or 1");
             L->comp = (int)value;
+            return OLB_OK;
+        case OLB_OPT_STOCHASTIC_ROUNDING:
+            if (value != 0 && value != 1) return fail(OLB_ERR_INVALID, "OLB_OPT_STOCHASTIC_ROUNDING takes 0 or 1");
+            L->sr = (int)value;
             return OLB_OK;
         case OLB_OPT_WARPS_PER_BLOCK:
             if (value < 1 || value > 8 || (value & (value - 1)))
@@ -456,6 +461,7 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     a.coll = L->p.coll;
     a.layout = L->p.layout;
     a.comp = L->comp;
+    a.sr = L->sr;
     a.warps_per_block = L->warps_per_block;
     a.kconst = L->p.storage == OLB_F64 ? static_cast<const void *>(&L->kd)
                                        : static_cast<const void *>(&L->kf);
@@ -464,6 +470,7 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     char *mem = static_cast<char *>(L->mem);
     for (int64_t s = 0; s < nsteps; ++s) {
         a.parity = (int)(L->t & 1);
+        a.t = L->t;
         if (L->p.layout == OLB_LAYOUT_AB) {
             a.src = mem + (size_t)(L->t & 1) * bytes;
             a.dst = mem + (size_t)((L->t + 1) & 1) * bytes;

@@ -69,6 +69,7 @@ void fill_desc(void *dst, const Member &m, const CollConst<C> &k) {
     d.t_base = m.t_base;
     d.g_base = m.g_base;
     d.g_end = m.g_end;
+    d.sr = L->sr;
     d.k = k;
     std::memcpy(dst, &d, sizeof d);
 }

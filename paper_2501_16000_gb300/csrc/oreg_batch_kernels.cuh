@@ -29,6 +29,7 @@ template <typename C> struct BatchDesc {
     long long t_base;     // lattice time when the global step counter was g_base
     long long g_base;     // first global step the lattice takes part in
     long long g_end;      // first global step it no longer takes part in
+    int sr;               // stochastic rounding of half formats
     CollConst<C> k;
 };
 
@@ -41,11 +42,14 @@ __device__ __forceinline__ void batch_item(const BatchDesc<typename Storage<S>::
     if constexpr (LAYOUT == 0) {
         const T *src = base + (size_t)(t & 1) * d.buf_elems;
         T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
-        item_ab<S, EQ, COLL, false>(src, dst, d.nx, d.ny, d.pitch, d.plane, y, seg, lane, d.k);
+        item_ab<S, EQ, COLL, false>(src, dst, d.nx, d.ny, d.pitch, d.plane, y, seg, lane, d.k, t,
+                                    d.sr != 0);
     } else if (t & 1) {
-        item_aa_odd<S, EQ, COLL, false>(base, d.nx, d.ny, d.pitch, d.plane, y, seg, lane, d.k);
+        item_aa_odd<S, EQ, COLL, false>(base, d.nx, d.ny, d.pitch, d.plane, y, seg, lane, d.k, t,
+                                        d.sr != 0);
     } else {
-        item_aa_even<S, EQ, COLL, false>(base, d.nx, d.pitch, d.plane, y, seg, lane, d.k);
+        item_aa_even<S, EQ, COLL, false>(base, d.nx, d.pitch, d.plane, y, seg, lane, d.k, t,
+                                         d.sr != 0);
     }
 }
 

@@ -52,16 +52,55 @@ template <> struct Storage<ST_F32> {
     __device__ static C dec(T v) { return v; }
     __device__ static T enc(C v) { return v; }
 };
+// Half formats also offer stochastic rounding: r is 16 uniform random bits;
+// the bits of v below the format's last mantissa bit (13 for f16, 16 for
+// bf16) get r added before truncation, so v rounds away from zero with
+// probability equal to its distance from the truncated value (exact for
+// normal numbers; values in the f16 subnormal range keep a bias below one
+// subnormal step).
+// f16 stores g * 2^8: the shifted populations are small (|g| ~ 1e-5 .. 1e-1
+// in the benchmarks), and the scale keeps them above the f16 subnormal
+// range (2^-14), where the format has fixed absolute resolution 2^-24.
+// Scaling by a power of two is exact.  |g| must stay below 65504 / 2^8 = 255.
 template <> struct Storage<ST_F16> {
     using T = __half; using C = float; static constexpr int V = 8;
-    __device__ static C dec(T v) { return __half2float(v); }
-    __device__ static T enc(C v) { return __float2half_rn(v); }
+    static constexpr float SCALE = 256.0f, INV_SCALE = 1.0f / 256.0f;
+    __device__ static C dec(T v) { return __half2float(v) * INV_SCALE; }
+    __device__ static T enc(C v) { return __float2half_rn(v * SCALE); }
+    __device__ static T enc_stochastic(C v, uint32_t r) {
+        return __float2half_rz(__uint_as_float(__float_as_uint(v * SCALE) + (r & 0x1FFFu)));
+    }
 };
 template <> struct Storage<ST_BF16> {
     using T = __nv_bfloat16; using C = float; static constexpr int V = 8;
     __device__ static C dec(T v) { return __bfloat162float(v); }
     __device__ static T enc(C v) { return __float2bfloat16_rn(v); }
+    __device__ static T enc_stochastic(C v, uint32_t r) {
+        return __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r & 0xFFFFu)));
+    }
 };
+
+// Counter-based random bits for stochastic rounding: a hash of the node and
+// time step (the 32-bit finalizer of MurmurHash3), then one multiplicative
+// hash per direction, (h * M_i) >> 16 with distinct odd M_i, whose upper
+// bits are well mixed.  The draws depend only on (x, y, t, i), so results do
+// not depend on how nodes are scheduled, batched or laid out.
+__device__ __forceinline__ uint32_t node_seed(int x, int y, long long t) {
+    uint32_t h = (uint32_t)x * 0x9E3779B1u;
+    h ^= (uint32_t)y * 0x85EBCA77u + 0x632BE5ABu;
+    h ^= (uint32_t)t * 0xC2B2AE3Du ^ (uint32_t)((unsigned long long)t >> 32) * 0x27D4EB2Fu;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ uint32_t direction_bits(uint32_t h, int i) {
+    const uint32_t m[9] = {0x9E3779B9u, 0x7F4A7C15u, 0xF39CC061u, 0x5851F42Du, 0xC8E2D8F5u,
+                           0x2545F491u, 0xB5297A4Du, 0x68E31DA5u, 0x1B56C4E9u};
+    return (h * m[i]) >> 16;
+}
 
 // 16-byte vector of V stored elements.
 template <int S> struct Vec {
@@ -237,41 +276,64 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
 // idle but still take part in the shuffles.
 // ---------------------------------------------------------------------------
 
-// Pull: out[j] = value at x - CX (periodic in x) of node x = xb + j, read from
-// the row at rowp.  NC selects the read-only data path (A-B layout).
+// Pull, in two phases so that a warp has all nine row fetches in flight
+// before it uses any of them:
+//   fetch_row: the lane's 16-byte vector at xb plus the one halo element the
+//              shift needs from outside the warp (or across the periodic wrap);
+//   shift_row: decode and move each value one node along x with shuffles, so
+//              that out[j] = value at x - CX (periodic) of node x = xb + j.
+// NC selects the read-only data path (A-B layout).
+template <int S> struct RawRow {
+    Vec<S> v;
+    typename Storage<S>::T halo;  // left (CX = +1) or right (CX = -1) neighbour
+    typename Storage<S>::T wrap;  // CX = -1: value at x = 0 for node nx - 1
+};
+
 template <int S, int CX, bool NC>
-__device__ __forceinline__ void load_row_shifted(const typename Storage<S>::T *rowp, int xb,
-                                                 int nx, int lane,
-                                                 typename Storage<S>::C out[Storage<S>::V]) {
+__device__ __forceinline__ RawRow<S> fetch_row(const typename Storage<S>::T *rowp, int xb, int nx,
+                                               int lane) {
+    using ST = Storage<S>;
+    constexpr int V = ST::V;
+    RawRow<S> r;
+    r.v.raw = make_uint4(0, 0, 0, 0);
+    r.halo = typename ST::T(0.0f);
+    r.wrap = typename ST::T(0.0f);
+    if (xb < nx) {
+        r.v = NC ? ld_vec_nc<S>(rowp + xb) : ld_vec<S>(rowp + xb);
+        if constexpr (CX == 1) {
+            if (lane == 0 || xb == 0) r.halo = rowp[xb == 0 ? nx - 1 : xb - 1];
+        } else if constexpr (CX == -1) {
+            if (lane == 31 && xb + V < nx) r.halo = rowp[xb + V];
+            if (xb + V >= nx) r.wrap = rowp[0];
+        }
+    }
+    return r;
+}
+
+template <int S, int CX>
+__device__ __forceinline__ void shift_row(const RawRow<S> &r, int xb, int nx, int lane,
+                                          typename Storage<S>::C out[Storage<S>::V]) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const bool active = xb < nx;
     C a[V];
-    if (active) {
-        Vec<S> v = NC ? ld_vec_nc<S>(rowp + xb) : ld_vec<S>(rowp + xb);
 #pragma unroll
-        for (int j = 0; j < V; ++j) a[j] = ST::dec(v.e[j]);
-    } else {
-#pragma unroll
-        for (int j = 0; j < V; ++j) a[j] = C(0);
-    }
+    for (int j = 0; j < V; ++j) a[j] = ST::dec(r.v.e[j]);
     if constexpr (CX == 0) {
 #pragma unroll
         for (int j = 0; j < V; ++j) out[j] = a[j];
     } else if constexpr (CX == 1) {
         // left neighbour of the lane's first node
         C left = __shfl_up_sync(0xffffffffu, a[V - 1], 1);
-        if (active && (lane == 0 || xb == 0)) left = ST::dec(rowp[xb == 0 ? nx - 1 : xb - 1]);
+        if (xb < nx && (lane == 0 || xb == 0)) left = ST::dec(r.halo);
         out[0] = left;
 #pragma unroll
         for (int j = 1; j < V; ++j) out[j] = a[j - 1];
     } else {
         // right neighbour of the lane's last node; node nx-1 wraps to x = 0
         C right = __shfl_down_sync(0xffffffffu, a[0], 1);
-        if (active && lane == 31 && xb + V < nx) right = ST::dec(rowp[xb + V]);
-        C wrapv = C(0);
-        if (active && xb + V >= nx) wrapv = ST::dec(rowp[0]);
+        if (xb < nx && lane == 31 && xb + V < nx) right = ST::dec(r.halo);
+        const C wrapv = ST::dec(r.wrap);
 #pragma unroll
         for (int j = 0; j < V - 1; ++j) out[j] = a[j + 1];
         out[V - 1] = right;
@@ -281,57 +343,76 @@ __device__ __forceinline__ void load_row_shifted(const typename Storage<S>::T *r
     }
 }
 
-// Push: the value p[j] of node x = xb + j goes to position x + CX (periodic)
-// of the row at rowp.  Each position is written exactly once, by the lane
-// that owns the node the value comes from; positions past nx (row padding)
-// may receive garbage.
+// Shuffles of raw stored elements (2, 4 or 8 bytes).
+template <typename T>
+__device__ __forceinline__ T shfl_up_raw(T v, int d) {
+    if constexpr (sizeof(T) == 2) {
+        unsigned short b;
+        memcpy(&b, &v, 2);
+        b = (unsigned short)__shfl_up_sync(0xffffffffu, (unsigned)b, d);
+        memcpy(&v, &b, 2);
+        return v;
+    } else {
+        return __shfl_up_sync(0xffffffffu, v, d);
+    }
+}
+template <typename T>
+__device__ __forceinline__ T shfl_down_raw(T v, int d) {
+    if constexpr (sizeof(T) == 2) {
+        unsigned short b;
+        memcpy(&b, &v, 2);
+        b = (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)b, d);
+        memcpy(&v, &b, 2);
+        return v;
+    } else {
+        return __shfl_down_sync(0xffffffffu, v, d);
+    }
+}
+
+// Push of already encoded elements: e[j] of node x = xb + j goes to position
+// x + CX (periodic) of the row at rowp.  Each position is written exactly
+// once, by the lane that owns the node the value comes from; positions past
+// nx (row padding) may receive any of the lane's values.
 template <int S, int CX>
-__device__ __forceinline__ void store_row_shifted(typename Storage<S>::T *rowp, int xb, int nx,
-                                                  int lane,
-                                                  const typename Storage<S>::C p[Storage<S>::V]) {
-    using ST = Storage<S>;
-    using C = typename ST::C;
-    constexpr int V = ST::V;
+__device__ __forceinline__ void store_row_shifted_raw(typename Storage<S>::T *rowp, int xb, int nx,
+                                                      int lane,
+                                                      const typename Storage<S>::T e[Storage<S>::V]) {
+    using T = typename Storage<S>::T;
+    constexpr int V = Storage<S>::V;
     const bool active = xb < nx;
     if constexpr (CX == 0) {
         if (active) {
             Vec<S> v;
 #pragma unroll
-            for (int j = 0; j < V; ++j) v.e[j] = ST::enc(p[j]);
+            for (int j = 0; j < V; ++j) v.e[j] = e[j];
             st_vec<S>(rowp + xb, v);
         }
     } else if constexpr (CX == 1) {
-        // position xb + j receives node xb + j - 1
-        const C from_left = __shfl_up_sync(0xffffffffu, p[V - 1], 1);
+        const T from_left = shfl_up_raw(e[V - 1], 1);
         if (active) {
             Vec<S> v;
-            v.e[0] = ST::enc(from_left);
+            v.e[0] = from_left;
 #pragma unroll
-            for (int j = 1; j < V; ++j) v.e[j] = ST::enc(p[j - 1]);
-            const bool first_foreign = (lane == 0) || (xb == 0);
-            if (!first_foreign) {
+            for (int j = 1; j < V; ++j) v.e[j] = e[j - 1];
+            if (!(lane == 0 || xb == 0)) {
                 st_vec<S>(rowp + xb, v);
             } else {
 #pragma unroll
                 for (int j = 1; j < V; ++j) rowp[xb + j] = v.e[j];
             }
-            // values whose target lies outside this lane's vector
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                const int x = xb + j;
-                if (x == nx - 1) rowp[0] = ST::enc(p[j]);
-            }
-            if (lane == 31 && xb + V < nx) rowp[xb + V] = ST::enc(p[V - 1]);
+            for (int j = 0; j < V; ++j)
+                if (xb + j == nx - 1) rowp[0] = e[j];
+            if (lane == 31 && xb + V < nx) rowp[xb + V] = e[V - 1];
         }
     } else {
-        // position xb + j receives node xb + j + 1
-        const C from_right = __shfl_down_sync(0xffffffffu, p[0], 1);
+        const T from_right = shfl_down_raw(e[0], 1);
         if (active) {
             Vec<S> v;
 #pragma unroll
-            for (int j = 0; j < V - 1; ++j) v.e[j] = ST::enc(p[j + 1]);
-            v.e[V - 1] = ST::enc(from_right);
-            const bool has_row_end = xb + V > nx - 1;           // holds position nx-1
+            for (int j = 0; j < V - 1; ++j) v.e[j] = e[j + 1];
+            v.e[V - 1] = from_right;
+            const bool has_row_end = xb + V > nx - 1;
             const bool last_foreign = (lane == 31) && (xb + V < nx);
             if (!has_row_end && !last_foreign) {
                 st_vec<S>(rowp + xb, v);
@@ -343,9 +424,8 @@ __device__ __forceinline__ void store_row_shifted(typename Storage<S>::T *rowp, 
                     if (!foreign) rowp[x] = v.e[j];
                 }
             }
-            // node xb's value goes to position xb - 1 (wrapping at the row start)
-            if (xb == 0) rowp[nx - 1] = ST::enc(p[0]);
-            else if (lane == 0) rowp[xb - 1] = ST::enc(p[0]);
+            if (xb == 0) rowp[nx - 1] = e[0];
+            else if (lane == 0) rowp[xb - 1] = e[0];
         }
     }
 }

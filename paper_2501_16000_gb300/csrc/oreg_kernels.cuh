@@ -17,16 +17,41 @@ namespace oreg {
 // dst at x.
 // ---------------------------------------------------------------------------
 template <int S, int I, bool AA_ODD>
-__device__ __forceinline__ void pull_plane(const typename Storage<S>::T *base, size_t plane,
-                                           int pitch, int y, int ny, int xb, int nx, int lane,
-                                           typename Storage<S>::C out[Storage<S>::V]) {
+__device__ __forceinline__ RawRow<S> fetch_plane(const typename Storage<S>::T *base, size_t plane,
+                                                 int pitch, int y, int ny, int xb, int nx,
+                                                 int lane) {
     // A-B: population i at x comes from plane i at x - c_i.
     // AA odd step: it comes from plane opp(i) at x - c_i (written there by the
     // preceding even step).
     constexpr int P = AA_ODD ? opp_of(I) : I;
     const int ys = wrap_row(y - cy_of(I), ny);
-    load_row_shifted<S, cx_of(I), !AA_ODD>(base + P * plane + (size_t)ys * pitch, xb, nx, lane,
-                                            out);
+    return fetch_row<S, cx_of(I), !AA_ODD>(base + P * plane + (size_t)ys * pitch, xb, nx, lane);
+}
+
+// Gathers the pre-collision populations of the warp's 32*V nodes: all nine
+// row fetches are issued before any is decoded.
+template <int S, bool AA_ODD>
+__device__ __forceinline__ void pull_all(const typename Storage<S>::T *base, size_t plane,
+                                         int pitch, int y, int ny, int xb, int nx, int lane,
+                                         typename Storage<S>::C f[9][Storage<S>::V]) {
+    const RawRow<S> r0 = fetch_plane<S, 0, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    const RawRow<S> r1 = fetch_plane<S, 1, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    const RawRow<S> r2 = fetch_plane<S, 2, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    const RawRow<S> r3 = fetch_plane<S, 3, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    const RawRow<S> r4 = fetch_plane<S, 4, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    const RawRow<S> r5 = fetch_plane<S, 5, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    const RawRow<S> r6 = fetch_plane<S, 6, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    const RawRow<S> r7 = fetch_plane<S, 7, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    const RawRow<S> r8 = fetch_plane<S, 8, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
+    shift_row<S, cx_of(0)>(r0, xb, nx, lane, f[0]);
+    shift_row<S, cx_of(1)>(r1, xb, nx, lane, f[1]);
+    shift_row<S, cx_of(2)>(r2, xb, nx, lane, f[2]);
+    shift_row<S, cx_of(3)>(r3, xb, nx, lane, f[3]);
+    shift_row<S, cx_of(4)>(r4, xb, nx, lane, f[4]);
+    shift_row<S, cx_of(5)>(r5, xb, nx, lane, f[5]);
+    shift_row<S, cx_of(6)>(r6, xb, nx, lane, f[6]);
+    shift_row<S, cx_of(7)>(r7, xb, nx, lane, f[7]);
+    shift_row<S, cx_of(8)>(r8, xb, nx, lane, f[8]);
 }
 
 // Row padding (positions nx .. pitch-1 of the last vector of a row) is kept
@@ -39,6 +64,31 @@ __device__ __forceinline__ void zero_padding(typename Storage<S>::C f[9][Storage
         if (xb + j >= nx)
 #pragma unroll
             for (int i = 0; i < 9; ++i) f[i][j] = typename Storage<S>::C(0);
+}
+
+// Encodes the post-collision values to the storage format: round to nearest,
+// or (half formats, sr) stochastically with counter-based bits per node,
+// time step and direction.
+template <int S>
+__device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Storage<S>::V],
+                                           typename Storage<S>::T e[9][Storage<S>::V], int xb,
+                                           int y, long long t, bool sr) {
+    using ST = Storage<S>;
+    if constexpr (S == ST_F16 || S == ST_BF16) {
+        if (sr) {
+#pragma unroll
+            for (int j = 0; j < ST::V; ++j) {
+                const uint32_t h = node_seed(xb + j, y, t);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) e[i][j] = ST::enc_stochastic(f[i][j], direction_bits(h, i));
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j < ST::V; ++j) e[i][j] = ST::enc(f[i][j]);
 }
 
 template <int S, int EQ, int COLL, bool COMP>
@@ -61,33 +111,28 @@ template <int S, int EQ, int COLL, bool COMP>
 __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict__ src,
                                         typename Storage<S>::T *__restrict__ dst, int nx, int ny,
                                         int pitch, size_t plane, int y, int seg, int lane,
-                                        const CollConst<typename Storage<S>::C> &k) {
+                                        const CollConst<typename Storage<S>::C> &k, long long t,
+                                        bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
     const int xb = seg * 32 * V + lane * V;
 
     C f[9][V];
-    pull_plane<S, 0, false>(src, plane, pitch, y, ny, xb, nx, lane, f[0]);
-    pull_plane<S, 1, false>(src, plane, pitch, y, ny, xb, nx, lane, f[1]);
-    pull_plane<S, 2, false>(src, plane, pitch, y, ny, xb, nx, lane, f[2]);
-    pull_plane<S, 3, false>(src, plane, pitch, y, ny, xb, nx, lane, f[3]);
-    pull_plane<S, 4, false>(src, plane, pitch, y, ny, xb, nx, lane, f[4]);
-    pull_plane<S, 5, false>(src, plane, pitch, y, ny, xb, nx, lane, f[5]);
-    pull_plane<S, 6, false>(src, plane, pitch, y, ny, xb, nx, lane, f[6]);
-    pull_plane<S, 7, false>(src, plane, pitch, y, ny, xb, nx, lane, f[7]);
-    pull_plane<S, 8, false>(src, plane, pitch, y, ny, xb, nx, lane, f[8]);
+    pull_all<S, false>(src, plane, pitch, y, ny, xb, nx, lane, f);
 
     collide_vec<S, EQ, COLL, COMP>(f, k);
 
     if (xb < nx) {
         if (xb + V > nx) zero_padding<S>(f, xb, nx);
+        typename ST::T e[9][V];
+        encode_vec<S>(f, e, xb, y, t, sr);
         typename ST::T *out = dst + (size_t)y * pitch + xb;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             Vec<S> v;
 #pragma unroll
-            for (int j = 0; j < V; ++j) v.e[j] = ST::enc(f[i][j]);
+            for (int j = 0; j < V; ++j) v.e[j] = e[i][j];
             st_vec<S>(out + i * plane, v);
         }
     }
@@ -97,11 +142,12 @@ template <int S, int EQ, int COLL, bool COMP>
 __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *__restrict__ src,
                                                  typename Storage<S>::T *__restrict__ dst, int nx,
                                                  int ny, int pitch, size_t plane, int segs,
-                                                 const CollConst<typename Storage<S>::C> k) {
+                                                 const CollConst<typename Storage<S>::C> k,
+                                                 long long t, bool sr) {
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (item >= (long long)ny * segs) return;  // warp-uniform
     item_ab<S, EQ, COLL, COMP>(src, dst, nx, ny, pitch, plane, (int)(item / segs),
-                               (int)(item % segs), threadIdx.x & 31, k);
+                               (int)(item % segs), threadIdx.x & 31, k, t, sr);
 }
 
 // ---------------------------------------------------------------------------
@@ -114,7 +160,8 @@ __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *_
 template <int S, int EQ, int COLL, bool COMP>
 __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, int pitch,
                                              size_t plane, int y, int seg, int lane,
-                                             const CollConst<typename Storage<S>::C> &k) {
+                                             const CollConst<typename Storage<S>::C> &k,
+                                             long long t, bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
@@ -130,11 +177,13 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
     }
     collide_vec<S, EQ, COLL, COMP>(f, k);
     if (xb + V > nx) zero_padding<S>(f, xb, nx);
+    typename ST::T e[9][V];
+    encode_vec<S>(f, e, xb, y, t, sr);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         Vec<S> v;
 #pragma unroll
-        for (int j = 0; j < V; ++j) v.e[j] = ST::enc(f[i][j]);
+        for (int j = 0; j < V; ++j) v.e[j] = e[i][j];
         st_vec<S>(row + opp_of(i) * plane, v);
     }
 }
@@ -142,63 +191,60 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
 template <int S, int EQ, int COLL, bool COMP>
 __global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A, int nx, int ny,
                                                       int pitch, size_t plane, int segs,
-                                                      const CollConst<typename Storage<S>::C> k) {
+                                                      const CollConst<typename Storage<S>::C> k,
+                                                      long long t, bool sr) {
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (item >= (long long)ny * segs) return;
     item_aa_even<S, EQ, COLL, COMP>(A, nx, pitch, plane, (int)(item / segs), (int)(item % segs),
-                                    threadIdx.x & 31, k);
+                                    threadIdx.x & 31, k, t, sr);
 }
 
 template <int S, int I>
 __device__ __forceinline__ void push_plane(typename Storage<S>::T *A, size_t plane, int pitch,
                                            int y, int ny, int xb, int nx, int lane,
-                                           const typename Storage<S>::C p[Storage<S>::V]) {
+                                           const typename Storage<S>::T p[Storage<S>::V]) {
     const int yd = wrap_row(y + cy_of(I), ny);
-    store_row_shifted<S, cx_of(I)>(A + I * plane + (size_t)yd * pitch, xb, nx, lane, p);
+    store_row_shifted_raw<S, cx_of(I)>(A + I * plane + (size_t)yd * pitch, xb, nx, lane, p);
 }
 
 template <int S, int EQ, int COLL, bool COMP>
 __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, int ny, int pitch,
                                             size_t plane, int y, int seg, int lane,
-                                            const CollConst<typename Storage<S>::C> &k) {
+                                            const CollConst<typename Storage<S>::C> &k,
+                                            long long t, bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
     const int xb = seg * 32 * V + lane * V;
 
     C f[9][V];
-    pull_plane<S, 0, true>(A, plane, pitch, y, ny, xb, nx, lane, f[0]);
-    pull_plane<S, 1, true>(A, plane, pitch, y, ny, xb, nx, lane, f[1]);
-    pull_plane<S, 2, true>(A, plane, pitch, y, ny, xb, nx, lane, f[2]);
-    pull_plane<S, 3, true>(A, plane, pitch, y, ny, xb, nx, lane, f[3]);
-    pull_plane<S, 4, true>(A, plane, pitch, y, ny, xb, nx, lane, f[4]);
-    pull_plane<S, 5, true>(A, plane, pitch, y, ny, xb, nx, lane, f[5]);
-    pull_plane<S, 6, true>(A, plane, pitch, y, ny, xb, nx, lane, f[6]);
-    pull_plane<S, 7, true>(A, plane, pitch, y, ny, xb, nx, lane, f[7]);
-    pull_plane<S, 8, true>(A, plane, pitch, y, ny, xb, nx, lane, f[8]);
+    pull_all<S, true>(A, plane, pitch, y, ny, xb, nx, lane, f);
 
     collide_vec<S, EQ, COLL, COMP>(f, k);
     if (xb < nx && xb + V > nx) zero_padding<S>(f, xb, nx);
+    typename ST::T e[9][V];
+    encode_vec<S>(f, e, xb, y, t, sr);
 
-    push_plane<S, 0>(A, plane, pitch, y, ny, xb, nx, lane, f[0]);
-    push_plane<S, 1>(A, plane, pitch, y, ny, xb, nx, lane, f[1]);
-    push_plane<S, 2>(A, plane, pitch, y, ny, xb, nx, lane, f[2]);
-    push_plane<S, 3>(A, plane, pitch, y, ny, xb, nx, lane, f[3]);
-    push_plane<S, 4>(A, plane, pitch, y, ny, xb, nx, lane, f[4]);
-    push_plane<S, 5>(A, plane, pitch, y, ny, xb, nx, lane, f[5]);
-    push_plane<S, 6>(A, plane, pitch, y, ny, xb, nx, lane, f[6]);
-    push_plane<S, 7>(A, plane, pitch, y, ny, xb, nx, lane, f[7]);
-    push_plane<S, 8>(A, plane, pitch, y, ny, xb, nx, lane, f[8]);
+    push_plane<S, 0>(A, plane, pitch, y, ny, xb, nx, lane, e[0]);
+    push_plane<S, 1>(A, plane, pitch, y, ny, xb, nx, lane, e[1]);
+    push_plane<S, 2>(A, plane, pitch, y, ny, xb, nx, lane, e[2]);
+    push_plane<S, 3>(A, plane, pitch, y, ny, xb, nx, lane, e[3]);
+    push_plane<S, 4>(A, plane, pitch, y, ny, xb, nx, lane, e[4]);
+    push_plane<S, 5>(A, plane, pitch, y, ny, xb, nx, lane, e[5]);
+    push_plane<S, 6>(A, plane, pitch, y, ny, xb, nx, lane, e[6]);
+    push_plane<S, 7>(A, plane, pitch, y, ny, xb, nx, lane, e[7]);
+    push_plane<S, 8>(A, plane, pitch, y, ny, xb, nx, lane, e[8]);
 }
 
 template <int S, int EQ, int COLL, bool COMP>
 __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
                                                      int pitch, size_t plane, int segs,
-                                                     const CollConst<typename Storage<S>::C> k) {
+                                                     const CollConst<typename Storage<S>::C> k,
+                                                     long long t, bool sr) {
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (item >= (long long)ny * segs) return;
     item_aa_odd<S, EQ, COLL, COMP>(A, nx, ny, pitch, plane, (int)(item / segs), (int)(item % segs),
-                                   threadIdx.x & 31, k);
+                                   threadIdx.x & 31, k, t, sr);
 }
 
 // ---------------------------------------------------------------------------
@@ -216,13 +262,13 @@ template <int S> struct StepLaunch {
         if (a.layout == 0) {
             k_step_ab<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
                 static_cast<const T *>(a.src), static_cast<T *>(a.dst), a.nx, a.ny, a.pitch,
-                a.plane, segs, k);
+                a.plane, segs, k, a.t, a.sr != 0);
         } else if (a.parity == 0) {
             k_step_aa_even<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
-                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, k);
+                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, k, a.t, a.sr != 0);
         } else {
             k_step_aa_odd<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
-                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, k);
+                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, k, a.t, a.sr != 0);
         }
     }
 

@@ -25,6 +25,7 @@ struct olb_lattice {
     bool own_stream;
     int64_t t;            // time of the canonical state; -1 = uninitialised
     int comp;
+    int sr;               // stochastic rounding of half formats
     int warps_per_block;
     int num_sms;
     double *d_red;        // reduction partials + result (library scratch)

@@ -29,6 +29,8 @@ struct StepArgs {
     int segs;          // row segments of 32*V nodes per row
     int eq, coll, layout, parity;
     int comp;          // compensated conserved-moment sums (FP32 only)
+    int sr;            // stochastic rounding (half formats only)
+    long long t;       // time of the state being advanced
     int warps_per_block;
     const void *kconst;  // CollConst<C> of the storage's compute type
     cudaStream_t stream;

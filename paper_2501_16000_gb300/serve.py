@@ -1,0 +1,159 @@
+"""Continuous-batching request server for shear-wave and shock-tube solves.
+
+Requests (``workloads.Request``: arrival time, lattice, step count) arrive
+over wall-clock time.  Arrived requests wait in a FIFO queue and are admitted
+as soon as their population memory (``olb_required_bytes``) fits the HBM
+budget next to everything in flight; admitted requests join the running
+``BatchEngine`` and advance together with all other in-flight requests, one
+CUDA-graph round of K steps at a time, their states resident in HBM.  A
+request whose steps are done is read back (moments to host), removed and its
+memory freed, which may admit the next ones.  Latency is arrival -> result in
+host memory.
+
+``serve_serial`` replays the same trace with one plain FP32 single-lattice
+solve at a time (the baseline).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from .batch import BatchEngine, work_items
+from .engine import Lattice, required_bytes
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival_s: float
+    admitted_s: float
+    done_s: float
+    nodes: int
+    steps: int
+    case: str
+    fields: tuple | None = None
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.arrival_s
+
+
+def summarize(results, wall_s, label):
+    lat = np.array([r.latency_s for r in results])
+    work = sum(r.nodes * r.steps for r in results)
+    return {
+        "label": label,
+        "solves": len(results),
+        "wall_s": round(wall_s, 3),
+        "solves_per_s": round(len(results) / wall_s, 2) if wall_s > 0 else None,
+        "mlups": round(work / wall_s / 1e6, 1) if wall_s > 0 else None,
+        "p50_latency_s": round(float(np.percentile(lat, 50)), 4) if len(lat) else None,
+        "p99_latency_s": round(float(np.percentile(lat, 99)), 4) if len(lat) else None,
+        "max_latency_s": round(float(lat.max()), 4) if len(lat) else None,
+    }
+
+
+def _bytes(lat_case, storage, layout):
+    return required_bytes(nx=lat_case.nx, ny=lat_case.ny, tau=lat_case.tau,
+                          theta=lat_case.theta, eq=lat_case.eq, coll=lat_case.coll,
+                          storage=storage, layout=layout)
+
+
+class Server:
+    def __init__(self, storage="f16", layout="ab", budget_bytes=120e9, steps_per_launch=100,
+                 max_lattices=8192, max_items=1 << 24, warps_per_block=4, blocks_per_sm=0,
+                 keep_fields=True):
+        self.storage, self.layout = storage, layout
+        self.budget = float(budget_bytes)
+        self.keep_fields = keep_fields
+        self.engine = BatchEngine(storage, layout, max_lattices=max_lattices,
+                                  max_items=max_items, steps_per_launch=steps_per_launch,
+                                  warps_per_block=warps_per_block, blocks_per_sm=blocks_per_sm)
+        self.max_items = max_items
+        self.rounds = 0
+        self.peak_bytes = 0
+        self.peak_inflight = 0
+
+    def close(self):
+        self.engine.close()
+
+    def run(self, trace, time_scale: float = 1.0):
+        """Serves the trace in real time (arrival times scaled by time_scale);
+        returns (results, wall seconds)."""
+        eng = self.engine
+        pending = collections.deque(sorted(trace, key=lambda r: r.arrival_s))
+        queue = collections.deque()
+        inflight = {}           # rid -> (request, lattice, bytes, admitted_s)
+        in_bytes = 0
+        in_items = 0
+        results = []
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        while pending or queue or inflight:
+            t = now()
+            while pending and pending[0].arrival_s * time_scale <= t:
+                queue.append(pending.popleft())
+            # FIFO admission against the memory budget (and the item table)
+            while queue:
+                req = queue[0]
+                need = _bytes(req.lattice, self.storage, self.layout)
+                items = work_items(req.lattice.nx, req.lattice.ny, self.storage)
+                if need > self.budget:
+                    raise ValueError(f"request {req.rid} needs {need} B > budget")
+                if in_bytes + need > self.budget or in_items + items > self.max_items:
+                    break
+                queue.popleft()
+                lat = eng.new_lattice(req.lattice)
+                eng.add(lat, req.lattice.steps)
+                inflight[req.rid] = (req, lat, need, now())
+                in_bytes += need
+                in_items += items
+            self.peak_bytes = max(self.peak_bytes, in_bytes)
+            self.peak_inflight = max(self.peak_inflight, len(inflight))
+            if not inflight:
+                if pending:
+                    wait = pending[0].arrival_s * time_scale - now()
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                continue
+            eng.run(1)
+            eng.wait()
+            self.rounds += 1
+            for rid in [r for r, (_, lat, _, _) in inflight.items() if eng.remaining(lat) == 0]:
+                req, lat, need, adm = inflight.pop(rid)
+                fields = lat.moments() if self.keep_fields else None
+                eng.remove(lat)
+                lat.close()
+                in_bytes -= need
+                in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage)
+                results.append(Result(rid, req.arrival_s * time_scale, adm, now(),
+                                      req.lattice.nodes, req.lattice.steps, req.lattice.case,
+                                      fields))
+        return results, now()
+
+
+def serve_serial(trace, storage="f32", layout="ab", time_scale: float = 1.0, keep_fields=True):
+    """Baseline: FIFO, one plain single-lattice solve at a time."""
+    pending = collections.deque(sorted(trace, key=lambda r: r.arrival_s))
+    results = []
+    t0 = time.perf_counter()
+    now = lambda: time.perf_counter() - t0
+    while pending:
+        req = pending.popleft()
+        wait = req.arrival_s * time_scale - now()
+        if wait > 0:
+            time.sleep(wait)
+        c = req.lattice
+        start = now()
+        with Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, storage, layout) as lat:
+            lat.init_case(c)
+            lat.step(c.steps)
+            fields = lat.moments() if keep_fields else None
+            if not keep_fields:
+                lat.diagnostics()
+        results.append(Result(req.rid, req.arrival_s * time_scale, start, now(), c.nodes,
+                              c.steps, c.case, fields))
+    return results, now()

@@ -1,0 +1,59 @@
+"""Serving on the GPU: requests served with continuous batching (joining and
+leaving while others run, admission against a memory budget) give the same
+result, bitwise, as the same request solved alone."""
+import numpy as np
+import pytest
+
+from paper_2501_16000_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_16000_gb300 import build
+    build.build()
+
+
+def small_trace(n=14, seed=11):
+    return W.arrival_trace(n, rate_per_s=400.0, seed=seed, lo=8, hi=96, steps_lo=10,
+                           steps_hi=300)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_served_results_equal_alone(layout):
+    from paper_2501_16000_gb300.engine import Lattice
+    from paper_2501_16000_gb300.serve import Server
+    trace = small_trace()
+    srv = Server("f16", layout, budget_bytes=1e9, steps_per_launch=16)
+    results, wall = srv.run(trace)
+    srv.close()
+    assert len(results) == len(trace)
+    assert srv.peak_inflight > 1                     # work actually overlapped
+    by_id = {r.rid: r for r in results}
+    for req in trace:
+        c = req.lattice
+        with Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, "f16", layout) as lat:
+            lat.init_case(c)
+            lat.step(c.steps)
+            alone = lat.moments()
+        for a, b in zip(alone, by_id[req.rid].fields):
+            assert np.array_equal(a, b), req.rid
+        assert by_id[req.rid].latency_s >= 0
+
+
+def test_admission_respects_the_budget():
+    from paper_2501_16000_gb300.engine import required_bytes
+    from paper_2501_16000_gb300.serve import Server
+    trace = small_trace(n=10, seed=3)
+    sizes = [required_bytes(nx=r.lattice.nx, ny=r.lattice.ny, tau=r.lattice.tau,
+                            storage="f16", layout="ab") for r in trace]
+    budget = 2 * max(sizes)
+    srv = Server("f16", "ab", budget_bytes=budget, steps_per_launch=16)
+    results, _ = srv.run(trace)
+    srv.close()
+    assert len(results) == len(trace)
+    assert srv.peak_bytes <= budget
