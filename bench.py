@@ -47,6 +47,12 @@ def parse_args():
     ap.add_argument("--comp", type=int, default=0, help="OLB_OPT_COMPENSATED (FP32)")
     ap.add_argument("--warps", type=int, default=4, help="OLB_OPT_WARPS_PER_BLOCK")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extended", action="store_true",
+                    help="skip the batched, serving and precision sections")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--decay-samples", type=int, default=12)
+    ap.add_argument("--serve-count", type=int, default=300)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-side", type=int, default=1024)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -323,11 +329,17 @@ def run_native(args):
                "note": f"one solve of {K} steps: olb_init_fields from pinned host fields, "
                        f"olb_step, olb_moments to pinned host arrays"}
 
+    lat.close()
+    extra = {}
+    if rank == 0 and not args.no_extended:
+        extra["precision_vs_fp64"] = precision_section(args)
+        extra["batched"] = batched_section(args)
+        extra["serving"] = serving_section(args, extra["batched"])
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, case, args.cpu_seconds)
 
-    lat.close()
     if rank == 0:
         line = {
             "metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
@@ -349,10 +361,127 @@ def run_native(args):
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": launches,
+            **extra,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def batched_section(args):
+    """Config 4: 512 independent uneven lattices, FP16 storage (stochastic
+    rounding) / FP32 compute, autotuned batch, one CUDA-graph replay per 100
+    steps; against serial plain FP32 single-lattice solves of the same set."""
+    import numpy as np
+    import torch
+    from paper_2501_16000_gb300 import workloads as W
+    from paper_2501_16000_gb300.analysis import measure_decay
+    from paper_2501_16000_gb300.batch import BatchEngine, autotune, work_items
+    from paper_2501_16000_gb300.engine import Lattice
+    steps, K = args.batch_steps, 100
+    cases = W.batch_mix(count=args.batch_count, seed=1, steps=steps)
+    nodes = sum(c.nodes for c in cases)
+    tuned = autotune(cases, "f16", steps=20, use_cache=False)
+    items = sum(work_items(c.nx, c.ny, "f16") for c in cases)
+    with BatchEngine("f16", tuned["layout"], max_lattices=len(cases), max_items=items,
+                     steps_per_launch=K, warps_per_block=tuned["warps_per_block"],
+                     blocks_per_sm=tuned["blocks_per_sm"]) as eng:
+        # warm-up solve (graph capture), then the timed solve on fresh states
+        for rep in range(2):
+            lats = [eng.new_lattice(c) for c in cases]
+            for lat in lats:
+                eng.add(lat, steps)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            eng.run((steps + K - 1) // K)
+            eng.wait()
+            dt = time.perf_counter() - t0
+            for lat in lats:
+                lat.close()
+    # serial plain FP32: the same lattices one after another (states created
+    # and initialised outside the timed region, as for the batch)
+    ser = [Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, "f32", "ab") for c in cases]
+    for lat, c in zip(ser, cases):
+        lat.init_case(c)
+    ser[0].step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for lat in ser:
+        lat.step(steps)
+    torch.cuda.synchronize()
+    dt_ser = time.perf_counter() - t0
+    for lat in ser:
+        lat.close()
+    # decay-rate error of F16 (stochastic rounding) vs FP64 on shear lattices of the mix
+    shear = [c for c in cases if c.case == "shear"][: args.decay_samples]
+    errs = []
+    for c in shear:
+        g = {}
+        for st in ("f64", "f16"):
+            with Lattice(c.nx, c.ny, c.tau, c.theta, storage=st, layout="ab") as lat:
+                lat.init_case(c)
+                g[st] = measure_decay(lat, c, steps, every=20)[0]
+        errs.append(abs(g["f16"] / g["f64"] - 1))
+    errs = np.array(errs)
+    return {
+        "workload": f"{len(cases)} lattices, sides log-uniform [32,1024] (seed 1), tau U[0.51,1], "
+                    f"u0 U[0.01,0.1], shear/shock 50/50, {steps} steps each, FP16 storage "
+                    f"(stochastic rounding) / FP32 compute, graph replay per {K} steps",
+        "nodes": nodes, "solves_per_s": round(len(cases) / dt, 2), "seconds": round(dt, 4),
+        "mlups": round(nodes * steps / dt / 1e6, 1), "tuned": tuned,
+        "baseline_fp32_serial": {"solves_per_s": round(len(cases) / dt_ser, 2),
+                                 "seconds": round(dt_ser, 4),
+                                 "mlups": round(nodes * steps / dt_ser / 1e6, 1)},
+        "speedup_vs_fp32_serial": round(dt_ser / dt, 2),
+        "decay_rate_error_vs_fp64": {"cases": len(errs), "max": float(f"{errs.max():.3e}"),
+                                     "median": float(f"{np.median(errs):.3e}"),
+                                     "le_1e-4": int((errs <= 1e-4).sum())},
+    }
+
+
+def serving_section(args, batched):
+    """Config 5: Poisson arrivals at ~80% of the measured batched capacity,
+    sides 64..2048, steps 100..10000, admission against a 120 GB budget,
+    continuous batching (FP16, stochastic rounding); vs serial FP32 solves."""
+    import numpy as np
+    from paper_2501_16000_gb300 import workloads as W
+    from paper_2501_16000_gb300.serve import Server, serve_serial, summarize
+    unit = W.arrival_trace(args.serve_count, rate_per_s=1.0, seed=2)
+    mean_work = float(np.mean([r.lattice.nodes * r.lattice.steps for r in unit]))
+    capacity = batched["mlups"] * 1e6 / mean_work            # requests per second
+    rate = 0.8 * capacity
+    srv = Server("f16", batched["tuned"]["layout"], budget_bytes=120e9, steps_per_launch=100,
+                 warps_per_block=batched["tuned"]["warps_per_block"],
+                 blocks_per_sm=batched["tuned"]["blocks_per_sm"])
+    res, wall = srv.run(unit, time_scale=1.0 / rate)
+    stats = summarize(res, wall, "continuous batching, FP16 storage")
+    stats.update({"rounds": srv.rounds, "peak_inflight": srv.peak_inflight,
+                  "peak_gb": round(srv.peak_bytes / 1e9, 2)})
+    srv.close()
+    sres, swall = serve_serial(unit, "f32", "ab", time_scale=1.0 / rate)
+    return {"requests": len(unit), "rate_per_s": round(rate, 2),
+            "capacity_estimate_per_s": round(capacity, 2), "budget_gb": 120,
+            "served": stats, "baseline_fp32_serial": summarize(sres, swall, "serial FP32")}
+
+
+def precision_section(args):
+    """Error of each reduced-precision storage against the FP64 GPU run
+    (itself matched to the FP64 oracle by the parity tests) on a periodic
+    shear wave, max |f - f64| / max |f64| over all populations."""
+    import numpy as np
+    from paper_2501_16000_gb300 import workloads as W
+    from paper_2501_16000_gb300.engine import Lattice
+    side, steps = 1024, 500
+    c = W.large_shear(theta=1.0 / 3.0, seed=0, side=side, steps=steps)
+    f = {}
+    for st in ("f64", "f32", "f16", "bf16"):
+        with Lattice(c.nx, c.ny, c.tau, c.theta, storage=st, layout="ab") as lat:
+            lat.init_case(c)
+            lat.step(steps)
+            f[st] = lat.populations()
+    den = np.abs(f["f64"]).max()
+    return {"workload": f"{side}x{side} shear wave, tau={c.tau}, {steps} steps",
+            **{st: float(f"{np.abs(f[st] - f['f64']).max() / den:.3e}") for st in ("f32", "f16", "bf16")}}
 
 
 def lat_bytes(storage, N):

@@ -99,8 +99,9 @@ typedef enum {
        0 (default): plain sums.  Ignored by the other formats. */
     OLB_OPT_COMPENSATED = 1,
     /* warps per thread block of the stream-collide kernels: 1, 2, 4 or 8
-       (default 4).  Each warp updates 32*V consecutive nodes of one row,
-       V = 16 bytes / element size. */
+       (default 4).  A warp updates 32/W row segments of W*V consecutive
+       nodes, V = 16 bytes / element size and W the smallest power of two
+       <= 32 with W * V >= nx. */
     OLB_OPT_WARPS_PER_BLOCK = 2,
     /* 1 (default for OLB_F16_SHIFTED and OLB_BF16_SHIFTED): round the
        post-collision values to the half format stochastically, with random
@@ -211,7 +212,9 @@ typedef struct {
     int32_t layout;            /* olb_layout of every member */
     int32_t max_lattices;      /* descriptor capacity */
     int64_t max_items;         /* work-item capacity: sum over members of
-                                  ny * ceil(nx / (32 * 16 / element size)) */
+                                  ceil(ny / (32 / W)) * ceil(nx / (W * V)),
+                                  V = 16 / element size, W the smallest power
+                                  of two <= 32 with W * V >= nx */
     int32_t steps_per_launch;  /* K: time steps per graph replay (1..10000) */
     int32_t warps_per_block;   /* 1, 2, 4 or 8 */
     int32_t blocks_per_sm;     /* persistent grid = blocks_per_sm x SMs;

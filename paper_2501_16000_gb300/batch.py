@@ -21,9 +21,16 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 
 
 def work_items(nx: int, ny: int, storage: str) -> int:
-    """Warp work items (row segments of 32 * 16-byte vectors) of one lattice."""
+    """Warp work items of one lattice: a warp covers 32/W rows of W-lane row
+    segments, W the smallest power of two <= 32 whose W 16-byte vectors span
+    the row."""
     v = 16 // {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[storage]
-    return ny * math.ceil(nx / (32 * v))
+    vecs = math.ceil(nx / v)
+    lw = 0
+    while lw < 5 and (1 << lw) < vecs:
+        lw += 1
+    w = 1 << lw
+    return math.ceil(ny / (32 // w)) * math.ceil(nx / (w * v))
 
 
 class BatchEngine:

@@ -117,18 +117,19 @@ template <typename C>
 CollConst<C> make_const(const olb_params *p) {
     CollConst<C> k;
     const double th = p->eq == OLB_EQ_GUIDED ? p->theta : 1.0 / 3.0;
-    const double psi0[3] = {1.0 - th, 0.5 * th, 0.5 * th};
+    const double psi0[2] = {1.0 - th, 0.5 * th};
+    for (int a = 0; a < 2; ++a) split<C>(psi0[a], k.psi0[a], k.psi0_lo[a]);
+    // classes: rest (psi0 psi0), axis (psi0 psi+-), diagonal (psi+- psi+-)
+    const double w[3] = {psi0[0] * psi0[0], psi0[0] * psi0[1], psi0[1] * psi0[1]};
+    const int count[3] = {1, 4, 4};
     double corr_sum = 0.0;
-    for (int a = 0; a < 3; ++a) split<C>(psi0[a], k.psi0[a], k.psi0_lo[a]);
-    for (int i = 0; i < 9; ++i) {
-        const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
-        const double w = psi0[a] * psi0[b];
-        split<C>(w, k.w[i], k.w_lo[i]);
-        const C s = (C)(w * p->rho0);
-        const double corr = w * p->rho0 - (double)s;
-        k.shift[i] = s;
-        k.corr[i] = (C)corr;
-        corr_sum += corr;
+    for (int c = 0; c < 3; ++c) {
+        split<C>(w[c], k.w[c], k.w_lo[c]);
+        const C s = (C)(w[c] * p->rho0);
+        const double corr = w[c] * p->rho0 - (double)s;
+        k.shift[c] = s;
+        k.corr[c] = (C)corr;
+        corr_sum += count[c] * corr;
     }
     k.sum_corr = (C)corr_sum;
     k.rho0 = (C)p->rho0;
@@ -144,11 +145,12 @@ CollConst<double> make_const_f64_for(const olb_params *p) {
     CollConst<double> kd = make_const<double>(p);
     if (p->storage != OLB_F64) {
         const CollConst<float> kf = make_const<float>(p);
+        const int count[3] = {1, 4, 4};
         double corr_sum = 0.0;
-        for (int i = 0; i < 9; ++i) {
-            kd.shift[i] = (double)kf.shift[i];
-            kd.corr[i] = kd.w[i] * p->rho0 - kd.shift[i];
-            corr_sum += kd.corr[i];
+        for (int c = 0; c < 3; ++c) {
+            kd.shift[c] = (double)kf.shift[c];
+            kd.corr[c] = kd.w[c] * p->rho0 - kd.shift[c];
+            corr_sum += count[c] * kd.corr[c];
         }
         kd.sum_corr = corr_sum;
     }
@@ -235,7 +237,7 @@ olb_status reduce(olb_lattice *L, const ModeSpec &mode, double out[RED_QUANTITIE
     for (int q = 0; q < RED_QUANTITIES; ++q) out[q] = L->h_red[q];
     // the kernel sums the shifted values g; add the shifts of the finite nodes
     double sum_shift = 0.0;
-    for (int i = 0; i < 9; ++i) sum_shift += L->kd.shift[i];
+    for (int i = 0; i < 9; ++i) sum_shift += L->kd.shift[dcls(i)];
     const double n_finite = (double)L->p.nx * L->p.ny - out[3];
     out[0] += n_finite * sum_shift;
     return OLB_OK;
@@ -456,7 +458,8 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     a.ny = L->p.ny;
     a.pitch = L->pitch;
     a.plane = L->plane;
-    a.segs = (L->p.nx + 32 * L->V - 1) / (32 * L->V);
+    a.lw = segment_log2(L->p.nx, L->V);
+    a.segs = (L->p.nx + (L->V << a.lw) - 1) / (L->V << a.lw);
     a.eq = L->p.eq;
     a.coll = L->p.coll;
     a.layout = L->p.layout;

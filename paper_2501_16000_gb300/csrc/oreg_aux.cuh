@@ -31,11 +31,11 @@ __device__ __forceinline__ size_t canon_index(int i, int x, int y, const StateGe
 
 template <int S>
 __device__ __forceinline__ void canon_node(const typename Storage<S>::T *base, int x, int y,
-                                           const StateGeom &g, const double shift[9],
+                                           const StateGeom &g, const double shift[3],
                                            double f[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        f[i] = (double)Storage<S>::dec(base[canon_index<S>(i, x, y, g)]) + shift[i];
+        f[i] = (double)Storage<S>::dec(base[canon_index<S>(i, x, y, g)]) + shift[dcls(i)];
     }
 }
 
@@ -51,16 +51,18 @@ __device__ __forceinline__ void eq_dev_f64(double rho, double ux, double uy,
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
-            geq[i] = drho * (k.w[i] + k.w_lo[i]) +
-                     rho * (dpx[a] * (k.psi0[b] + dpy[b]) + k.psi0[a] * dpy[b]) + k.corr[i];
+            const int pa = cx_of(i) != 0, pb = cy_of(i) != 0, ci = dcls(i);
+            geq[i] = drho * (k.w[ci] + k.w_lo[ci]) +
+                     rho * (dpx[a] * (k.psi0[pb] + dpy[b]) + k.psi0[pa] * dpy[b]) + k.corr[ci];
         }
     } else {
         const double u2 = ux2 + uy2;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const double cu = cx_of(i) * ux + cy_of(i) * uy;
-            geq[i] = (k.w[i] + k.w_lo[i]) * (drho + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2)) +
-                     k.corr[i];
+            const int ci = dcls(i);
+            geq[i] = (k.w[ci] + k.w_lo[ci]) * (drho + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2)) +
+                     k.corr[ci];
         }
     }
 }
@@ -124,7 +126,7 @@ __global__ void k_set_canonical(typename Storage<S>::T *base, StateGeom g, int y
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         base[canon_index<S>(i, x, y, g)] =
-            Storage<S>::enc((typename Storage<S>::C)(in[i * cnt + n] - kd.shift[i]));
+            Storage<S>::enc((typename Storage<S>::C)(in[i * cnt + n] - kd.shift[dcls(i)]));
     }
 }
 
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Storage<S
     double nonfinite = 0.0;
     C sum_shift = 0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) sum_shift += (C)kd.shift[i];
+    for (int i = 0; i < 9; ++i) sum_shift += (C)kd.shift[dcls(i)];
     const long long N = (long long)g.nx * g.ny;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {

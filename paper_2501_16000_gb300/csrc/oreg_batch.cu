@@ -64,6 +64,7 @@ void fill_desc(void *dst, const Member &m, const CollConst<C> &k) {
     d.pitch = L->pitch;
     d.eq = L->p.eq;
     d.coll = L->p.coll;
+    d.lw = segment_log2(L->p.nx, L->V);
     d.plane = L->plane;
     d.buf_elems = L->buf_elems;
     d.t_base = m.t_base;
@@ -86,13 +87,13 @@ struct olb_batch {
     // device tables
     char *d_descs;
     int4 *d_items;
-    int *d_nitems;
+    int *d_groups;          // item offsets of the 8 (eq, coll, parity class) groups
     long long *d_g;
     // host mirrors
     std::vector<Member> members;
     std::vector<char> h_descs;
     std::vector<int4> h_items;
-    int *h_nitems;          // pinned
+    int *h_groups;          // pinned, 9 entries
     long long G;            // global step counter at the start of the next round
     bool captured;
     cudaGraph_t graph;
@@ -104,20 +105,29 @@ namespace {
 olb_status upload(olb_batch *b) {
     const size_t nm = b->members.size();
     b->h_descs.assign(nm * b->desc_size, 0);
-    b->h_items.clear();
+    std::vector<int4> per_group[8];
     for (size_t j = 0; j < nm; ++j) {
         const Member &m = b->members[j];
         const olb_lattice *L = m.lat;
         if (L->p.storage == OLB_F64) fill_desc<double>(&b->h_descs[j * b->desc_size], m, L->kd);
         else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf);
-        const int segs = (L->p.nx + 32 * L->V - 1) / (32 * L->V);
-        for (int y = 0; y < L->p.ny; ++y)
-            for (int s = 0; s < segs; ++s) b->h_items.push_back(make_int4((int)j, y, s, 0));
+        const int cls = (int)((m.t_base - m.g_base) & 1);
+        const int grp = (L->p.eq * 2 + L->p.coll) * 2 + cls;
+        const int lw = segment_log2(L->p.nx, L->V);
+        const int segs = (L->p.nx + (L->V << lw) - 1) / (L->V << lw);
+        const int rows = 32 >> lw;  // rows per warp item
+        for (int y = 0; y < L->p.ny; y += rows)
+            for (int s = 0; s < segs; ++s) per_group[grp].push_back(make_int4((int)j, y, s, 0));
     }
+    b->h_items.clear();
+    for (int q = 0; q < 8; ++q) {
+        b->h_groups[q] = (int)b->h_items.size();
+        b->h_items.insert(b->h_items.end(), per_group[q].begin(), per_group[q].end());
+    }
+    b->h_groups[8] = (int)b->h_items.size();
     if ((long long)b->h_items.size() > b->p.max_items)
         return bfail(OLB_ERR_NOMEM, "batch work items %zu exceed max_items %lld", b->h_items.size(),
                      (long long)b->p.max_items);
-    *b->h_nitems = (int)b->h_items.size();
     if (nm)
         B_CUDA(cudaMemcpyAsync(b->d_descs, b->h_descs.data(), b->h_descs.size(),
                                cudaMemcpyHostToDevice, b->stream),
@@ -126,9 +136,9 @@ olb_status upload(olb_batch *b) {
         B_CUDA(cudaMemcpyAsync(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(int4),
                                cudaMemcpyHostToDevice, b->stream),
                "uploading batch items");
-    B_CUDA(cudaMemcpyAsync(b->d_nitems, b->h_nitems, sizeof(int), cudaMemcpyHostToDevice,
+    B_CUDA(cudaMemcpyAsync(b->d_groups, b->h_groups, 9 * sizeof(int), cudaMemcpyHostToDevice,
                            b->stream),
-           "uploading item count");
+           "uploading item groups");
     // the host vectors may change on the next call
     B_CUDA(cudaStreamSynchronize(b->stream), "synchronising batch upload");
     return OLB_OK;
@@ -140,7 +150,7 @@ olb_status capture(olb_batch *b) {
     BatchLaunch a{};
     a.descs = b->d_descs;
     a.items = b->d_items;
-    a.n_items = b->d_nitems;
+    a.groups = b->d_groups;
     a.g = b->d_g;
     a.layout = b->p.layout;
     a.grid = b->grid;
@@ -220,13 +230,13 @@ olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out) {
     b->grid = per_sm * b->num_sms;
     e = cudaMalloc(&b->d_descs, (size_t)p->max_lattices * b->desc_size);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, (size_t)p->max_items * sizeof(int4));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_nitems, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_groups, 9 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_g, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_nitems, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_groups, 9 * sizeof(int));
     if (e != cudaSuccess) return bail(bcuda(e, "allocating batch tables"));
-    *b->h_nitems = 0;
+    for (int q = 0; q < 9; ++q) b->h_groups[q] = 0;
     e = cudaMemsetAsync(b->d_g, 0, sizeof(long long), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nitems, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_groups, 0, 9 * sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bail(bcuda(e, "clearing batch tables"));
     b->G = 0;
@@ -326,9 +336,9 @@ olb_status olb_batch_destroy(olb_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_descs) cudaFree(b->d_descs);
     if (b->d_items) cudaFree(b->d_items);
-    if (b->d_nitems) cudaFree(b->d_nitems);
+    if (b->d_groups) cudaFree(b->d_groups);
     if (b->d_g) cudaFree(b->d_g);
-    if (b->h_nitems) cudaFreeHost(b->h_nitems);
+    if (b->h_groups) cudaFreeHost(b->h_groups);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return st;

@@ -6,10 +6,10 @@
 // and equilibrium constants in a device descriptor.  A device-resident global
 // step counter g decides, per lattice, whether it is active in this launch
 // (g_base <= g < g_end) and at which local time t = t_base + (g - g_base),
-// which selects the A-B buffer or the AA parity.  K launches and one counter
-// increment are captured once in a CUDA graph; joining and leaving lattices
-// only rewrite the descriptor and item tables, so the graph is never
-// re-captured.
+// which selects the A-B buffer or the AA parity.  The launches of K steps and
+// one counter increment are captured once in a CUDA graph; joining and
+// leaving lattices only rewrite the descriptor, item and group tables, so the
+// graph is never re-captured.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,6 +24,7 @@ template <typename C> struct BatchDesc {
     void *mem;            // population memory (A-B: two buffers back to back)
     int nx, ny, pitch;
     int eq, coll;
+    int lw;               // log2 of the lanes per row segment
     size_t plane;         // elements per plane
     size_t buf_elems;     // elements per population buffer
     long long t_base;     // lattice time when the global step counter was g_base
@@ -33,63 +34,88 @@ template <typename C> struct BatchDesc {
     CollConst<C> k;
 };
 
-// One work item: x = descriptor index, y = row, z = row segment.
-template <int S, int LAYOUT, int EQ, int COLL>
-__device__ __forceinline__ void batch_item(const BatchDesc<typename Storage<S>::C> &d, long long t,
-                                           int y, int seg, int lane) {
-    using T = typename Storage<S>::T;
-    T *base = static_cast<T *>(d.mem);
-    if constexpr (LAYOUT == 0) {
-        const T *src = base + (size_t)(t & 1) * d.buf_elems;
-        T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
-        item_ab<S, EQ, COLL, false>(src, dst, d.nx, d.ny, d.pitch, d.plane, y, seg, lane, d.k, t,
-                                    d.sr != 0);
-    } else if (t & 1) {
-        item_aa_odd<S, EQ, COLL, false>(base, d.nx, d.ny, d.pitch, d.plane, y, seg, lane, d.k, t,
-                                        d.sr != 0);
-    } else {
-        item_aa_even<S, EQ, COLL, false>(base, d.nx, d.pitch, d.plane, y, seg, lane, d.k, t,
-                                         d.sr != 0);
-    }
-}
+// Work items are grouped on the host by (equilibrium, collision, parity
+// class): group = (eq * 2 + coll) * 2 + c, with c = (t_base - g_base) & 1 the
+// lattice's fixed offset between its own time and the global step, so that
+// at global step g every lattice of class c has time parity (g + c) & 1.
+// Each kernel below handles one (eq, coll) and, for the in-place layout, one
+// parity: one item body per kernel keeps register use at the single-lattice
+// kernels' level.  groups[0..8] are the item offsets of the 8 groups.
+enum { BATCH_AB = 0, BATCH_AA_EVEN = 1, BATCH_AA_ODD = 2 };
 
-template <int S, int LAYOUT>
-__global__ void __launch_bounds__(256)
+// 256 threads x 2 blocks per SM caps registers at 128 per thread: the
+// per-lattice constants come from the descriptor in global memory rather than
+// the parameter bank, and left to itself the compiler keeps them all in
+// registers (150-180 for half storage), halving occupancy; reloading a few
+// from L1 is cheaper (measured: 49 -> 63 GLUPS on 512 mixed FP16 lattices).
+template <int S, int KIND, int EQ, int COLL>
+__global__ void __launch_bounds__(256, 2)
     k_batch_step(const BatchDesc<typename Storage<S>::C> *__restrict__ descs,
-                 const int4 *__restrict__ items, const int *__restrict__ n_items,
+                 const int4 *__restrict__ items, const int *__restrict__ groups,
                  const long long *__restrict__ g_round, int k) {
+    using T = typename Storage<S>::T;
     const long long g = *g_round + k;
-    const int n = *n_items;
+    constexpr int combo = EQ * 2 + COLL;
+    int lo, hi;
+    if constexpr (KIND == BATCH_AB) {
+        lo = groups[combo * 2];
+        hi = groups[combo * 2 + 2];
+    } else {
+        const int c = (KIND == BATCH_AA_EVEN) ? (int)(g & 1) : (int)((g & 1) ^ 1);
+        lo = groups[combo * 2 + c];
+        hi = groups[combo * 2 + c + 1];
+    }
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
+    for (int w = lo + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < hi; w += warps) {
         const int4 it = items[w];
         const BatchDesc<typename Storage<S>::C> &d = descs[it.x];
         if (g < d.g_base || g >= d.g_end) continue;  // warp-uniform
         const long long t = d.t_base + (g - d.g_base);
-        const int sel = d.eq * 2 + d.coll;
-        if (sel == 0) batch_item<S, LAYOUT, EQ_GUIDED, COLL_OREG>(d, t, it.y, it.z, lane);
-        else if (sel == 1) batch_item<S, LAYOUT, EQ_GUIDED, COLL_BGK>(d, t, it.y, it.z, lane);
-        else if (sel == 2) batch_item<S, LAYOUT, EQ_POLY2, COLL_OREG>(d, t, it.y, it.z, lane);
-        else batch_item<S, LAYOUT, EQ_POLY2, COLL_BGK>(d, t, it.y, it.z, lane);
+        T *base = static_cast<T *>(d.mem);
+        if constexpr (KIND == BATCH_AB) {
+            const T *src = base + (size_t)(t & 1) * d.buf_elems;
+            T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
+            item_ab<S, EQ, COLL, false>(src, dst, d.nx, d.ny, d.pitch, d.plane, it.y, it.z, lane,
+                                        d.lw, d.k, t, d.sr != 0);
+        } else if constexpr (KIND == BATCH_AA_ODD) {
+            item_aa_odd<S, EQ, COLL, false>(base, d.nx, d.ny, d.pitch, d.plane, it.y, it.z, lane,
+                                            d.lw, d.k, t, d.sr != 0);
+        } else {
+            item_aa_even<S, EQ, COLL, false>(base, d.nx, d.ny, d.pitch, d.plane, it.y, it.z, lane,
+                                             d.lw, d.k, t, d.sr != 0);
+        }
     }
 }
 
 template <int S> struct BatchLaunchT {
-    static cudaError_t launch(const BatchLaunch &a) {
+    template <int KIND>
+    static cudaError_t launch_kind(const BatchLaunch &a) {
         using D = BatchDesc<typename Storage<S>::C>;
         const D *descs = static_cast<const D *>(a.descs);
-        if (a.layout == 0)
-            k_batch_step<S, 0><<<a.grid, a.block, 0, a.stream>>>(descs, a.items, a.n_items, a.g, a.k);
-        else
-            k_batch_step<S, 1><<<a.grid, a.block, 0, a.stream>>>(descs, a.items, a.n_items, a.g, a.k);
+        k_batch_step<S, KIND, EQ_GUIDED, COLL_OREG><<<a.grid, a.block, 0, a.stream>>>(
+            descs, a.items, a.groups, a.g, a.k);
+        k_batch_step<S, KIND, EQ_GUIDED, COLL_BGK><<<a.grid, a.block, 0, a.stream>>>(
+            descs, a.items, a.groups, a.g, a.k);
+        k_batch_step<S, KIND, EQ_POLY2, COLL_OREG><<<a.grid, a.block, 0, a.stream>>>(
+            descs, a.items, a.groups, a.g, a.k);
+        k_batch_step<S, KIND, EQ_POLY2, COLL_BGK><<<a.grid, a.block, 0, a.stream>>>(
+            descs, a.items, a.groups, a.g, a.k);
         return cudaGetLastError();
+    }
+    static cudaError_t launch(const BatchLaunch &a) {
+        if (a.layout == 0) return launch_kind<BATCH_AB>(a);
+        cudaError_t e = launch_kind<BATCH_AA_EVEN>(a);
+        if (e != cudaSuccess) return e;
+        return launch_kind<BATCH_AA_ODD>(a);
     }
     static int occupancy(int layout, int block) {
         int n = 0;
         cudaError_t e = layout == 0
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<S, 0>, block, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<S, 1>, block, 0);
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &n, k_batch_step<S, BATCH_AB, EQ_GUIDED, COLL_OREG>, block, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &n, k_batch_step<S, BATCH_AA_ODD, EQ_GUIDED, COLL_OREG>, block, 0);
         return e == cudaSuccess ? n : 0;
     }
 };

@@ -30,6 +30,11 @@ __host__ __device__ constexpr int opp_of(int i) {
 }
 // Component index of a velocity component: 0 -> 0, +1 -> 1, -1 -> 2.
 __host__ __device__ constexpr int kidx(int c) { return c == 0 ? 0 : (c > 0 ? 1 : 2); }
+// Symmetry class of a direction: 0 rest, 1 axis, 2 diagonal (the rest
+// weights, shifts and their corrections depend on the class only).
+__host__ __device__ constexpr int dcls(int i) {
+    return (cx_of(i) != 0 ? 1 : 0) + (cy_of(i) != 0 ? 1 : 0);
+}
 
 static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp");
 static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp");
@@ -130,13 +135,15 @@ __device__ __forceinline__ void st_vec(typename Storage<S>::T *p, const Vec<S> &
 // ---------------------------------------------------------------------------
 template <typename C> struct CollConst {
     C rho0;          // reference density of the shift
-    C psi0[3];       // 1-D rest factors: guided Psi_0(0) = 1 - theta, Psi_+-(0) = theta/2;
+    // Rest factors and weights by symmetry: index [c != 0] for the 1-D
+    // factors, [dcls(i)] (rest, axis, diagonal) for the per-direction values.
+    C psi0[2];       // 1-D rest factors: guided Psi_0(0) = 1 - theta, Psi_+-(0) = theta/2;
                      // poly2 W_0 = 1 - theta0, W_+- = theta0 / 2; rounded to C ...
-    C psi0_lo[3];    // ... plus the rounding remainder (hi + lo exact to ~2^-48)
-    C w[9];          // W_i = Psi_a(0) Psi_b(0) rounded to C ...
-    C w_lo[9];       // ... plus the rounding remainder
-    C shift[9];      // storage shift s_i (rest equilibrium rounded to C)
-    C corr[9];       // W_i rho0 - s_i (exact difference, rounded to C)
+    C psi0_lo[2];    // ... plus the rounding remainder (hi + lo exact to ~2^-48)
+    C w[3];          // W_i = Psi_a(0) Psi_b(0) rounded to C ...
+    C w_lo[3];       // ... plus the rounding remainder
+    C shift[3];      // storage shift s_i (rest equilibrium rounded to C)
+    C corr[3];       // W_i rho0 - s_i (exact difference, rounded to C)
     C sum_corr;      // sum_i corr_i
     C lam;           // 1 - 1/tau
     C inv_2th2;      // 1 / (2 theta^2), theta = lattice theta (guided) or theta0 (poly2)
@@ -226,12 +233,13 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
+            const int pa = cx_of(i) != 0, pb = cy_of(i) != 0, ci = dcls(i);
             // dPsi_a Psi_b + Psi_a(0) dPsi_b with Psi(0) = hi + lo
-            const C psib = k.psi0[b] + dpy[b];
+            const C psib = k.psi0[pb] + dpy[b];
             const C t = fma(dpx[a], psib,
-                            fma(dpx[a], k.psi0_lo[b], fma(k.psi0[a], dpy[b], k.psi0_lo[a] * dpy[b])));
-            const C vel = fma(rho, t, k.corr[i]);
-            geq[i] = fma(drho, k.w[i], fma(drho, k.w_lo[i], vel));
+                            fma(dpx[a], k.psi0_lo[pb], fma(k.psi0[pa], dpy[b], k.psi0_lo[pa] * dpy[b])));
+            const C vel = fma(rho, t, k.corr[ci]);
+            geq[i] = fma(drho, k.w[ci], fma(drho, k.w_lo[ci], vel));
         }
     } else {
         const C u2 = ux2 + uy2;
@@ -240,8 +248,9 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
             const C cu = C(cx_of(i)) * ux + C(cy_of(i)) * uy;
             const C poly = fma(C(3), cu, fma(C(4.5) * cu, cu, C(-1.5) * u2));
             const C rp = rho * poly;
-            const C vel = fma(rp, k.w[i], fma(rp, k.w_lo[i], k.corr[i]));
-            geq[i] = fma(drho, k.w[i], fma(drho, k.w_lo[i], vel));
+            const int ci = dcls(i);
+            const C vel = fma(rp, k.w[ci], fma(rp, k.w_lo[ci], k.corr[ci]));
+            geq[i] = fma(drho, k.w[ci], fma(drho, k.w_lo[ci], vel));
         }
     }
 
@@ -261,7 +270,7 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         for (int i = 0; i < 9; ++i) {
             const int ia = kidx(cx_of(i)), ib = kidx(cy_of(i));
             const C d = fma(X[ia] * X[ia] - Y[ib] * Y[ib], sxx, X[ia] * Y[ib] * two_sxy);
-            const C feq = k.shift[i] + geq[i];
+            const C feq = k.shift[dcls(i)] + geq[i];
             post[i] = fma(feq, a * d, geq[i]);
         }
     }
@@ -270,10 +279,12 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
 // ---------------------------------------------------------------------------
 // Warp-level shifted row-segment access.
 //
-// A warp owns 32*V consecutive nodes x = xb .. xb+V-1 per lane (xb = seg*32V +
-// lane*V) of one row; row storage has a pitch that is a multiple of V, so a
-// lane's V elements are one aligned 16-byte vector.  Lanes with xb >= nx are
-// idle but still take part in the shuffles.
+// A warp is split into 32/W segments of W lanes (W a power of two chosen
+// from the lattice width); each segment owns W*V consecutive nodes of one
+// row, x = xb .. xb+V-1 per lane (xb = seg*W*V + sub*V, sub = lane mod W).
+// Row storage has a pitch that is a multiple of V, so a lane's V elements are
+// one aligned 16-byte vector.  Shuffles run within the segment (width W).
+// Lanes with xb >= nx are idle but still take part in the shuffles.
 // ---------------------------------------------------------------------------
 
 // Pull, in two phases so that a warp has all nine row fetches in flight
@@ -291,7 +302,7 @@ template <int S> struct RawRow {
 
 template <int S, int CX, bool NC>
 __device__ __forceinline__ RawRow<S> fetch_row(const typename Storage<S>::T *rowp, int xb, int nx,
-                                               int lane) {
+                                               int sub, int W) {
     using ST = Storage<S>;
     constexpr int V = ST::V;
     RawRow<S> r;
@@ -301,9 +312,9 @@ __device__ __forceinline__ RawRow<S> fetch_row(const typename Storage<S>::T *row
     if (xb < nx) {
         r.v = NC ? ld_vec_nc<S>(rowp + xb) : ld_vec<S>(rowp + xb);
         if constexpr (CX == 1) {
-            if (lane == 0 || xb == 0) r.halo = rowp[xb == 0 ? nx - 1 : xb - 1];
+            if (sub == 0 || xb == 0) r.halo = rowp[xb == 0 ? nx - 1 : xb - 1];
         } else if constexpr (CX == -1) {
-            if (lane == 31 && xb + V < nx) r.halo = rowp[xb + V];
+            if (sub == W - 1 && xb + V < nx) r.halo = rowp[xb + V];
             if (xb + V >= nx) r.wrap = rowp[0];
         }
     }
@@ -311,7 +322,7 @@ __device__ __forceinline__ RawRow<S> fetch_row(const typename Storage<S>::T *row
 }
 
 template <int S, int CX>
-__device__ __forceinline__ void shift_row(const RawRow<S> &r, int xb, int nx, int lane,
+__device__ __forceinline__ void shift_row(const RawRow<S> &r, int xb, int nx, int sub, int W,
                                           typename Storage<S>::C out[Storage<S>::V]) {
     using ST = Storage<S>;
     using C = typename ST::C;
@@ -324,15 +335,15 @@ __device__ __forceinline__ void shift_row(const RawRow<S> &r, int xb, int nx, in
         for (int j = 0; j < V; ++j) out[j] = a[j];
     } else if constexpr (CX == 1) {
         // left neighbour of the lane's first node
-        C left = __shfl_up_sync(0xffffffffu, a[V - 1], 1);
-        if (xb < nx && (lane == 0 || xb == 0)) left = ST::dec(r.halo);
+        C left = __shfl_up_sync(0xffffffffu, a[V - 1], 1, W);
+        if (xb < nx && (sub == 0 || xb == 0)) left = ST::dec(r.halo);
         out[0] = left;
 #pragma unroll
         for (int j = 1; j < V; ++j) out[j] = a[j - 1];
     } else {
         // right neighbour of the lane's last node; node nx-1 wraps to x = 0
-        C right = __shfl_down_sync(0xffffffffu, a[0], 1);
-        if (xb < nx && lane == 31 && xb + V < nx) right = ST::dec(r.halo);
+        C right = __shfl_down_sync(0xffffffffu, a[0], 1, W);
+        if (xb < nx && sub == W - 1 && xb + V < nx) right = ST::dec(r.halo);
         const C wrapv = ST::dec(r.wrap);
 #pragma unroll
         for (int j = 0; j < V - 1; ++j) out[j] = a[j + 1];
@@ -345,27 +356,27 @@ __device__ __forceinline__ void shift_row(const RawRow<S> &r, int xb, int nx, in
 
 // Shuffles of raw stored elements (2, 4 or 8 bytes).
 template <typename T>
-__device__ __forceinline__ T shfl_up_raw(T v, int d) {
+__device__ __forceinline__ T shfl_up_raw(T v, int d, int w) {
     if constexpr (sizeof(T) == 2) {
         unsigned short b;
         memcpy(&b, &v, 2);
-        b = (unsigned short)__shfl_up_sync(0xffffffffu, (unsigned)b, d);
+        b = (unsigned short)__shfl_up_sync(0xffffffffu, (unsigned)b, d, w);
         memcpy(&v, &b, 2);
         return v;
     } else {
-        return __shfl_up_sync(0xffffffffu, v, d);
+        return __shfl_up_sync(0xffffffffu, v, d, w);
     }
 }
 template <typename T>
-__device__ __forceinline__ T shfl_down_raw(T v, int d) {
+__device__ __forceinline__ T shfl_down_raw(T v, int d, int w) {
     if constexpr (sizeof(T) == 2) {
         unsigned short b;
         memcpy(&b, &v, 2);
-        b = (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)b, d);
+        b = (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)b, d, w);
         memcpy(&v, &b, 2);
         return v;
     } else {
-        return __shfl_down_sync(0xffffffffu, v, d);
+        return __shfl_down_sync(0xffffffffu, v, d, w);
     }
 }
 
@@ -375,7 +386,7 @@ __device__ __forceinline__ T shfl_down_raw(T v, int d) {
 // nx (row padding) may receive any of the lane's values.
 template <int S, int CX>
 __device__ __forceinline__ void store_row_shifted_raw(typename Storage<S>::T *rowp, int xb, int nx,
-                                                      int lane,
+                                                      int sub, int W,
                                                       const typename Storage<S>::T e[Storage<S>::V]) {
     using T = typename Storage<S>::T;
     constexpr int V = Storage<S>::V;
@@ -388,13 +399,13 @@ __device__ __forceinline__ void store_row_shifted_raw(typename Storage<S>::T *ro
             st_vec<S>(rowp + xb, v);
         }
     } else if constexpr (CX == 1) {
-        const T from_left = shfl_up_raw(e[V - 1], 1);
+        const T from_left = shfl_up_raw(e[V - 1], 1, W);
         if (active) {
             Vec<S> v;
             v.e[0] = from_left;
 #pragma unroll
             for (int j = 1; j < V; ++j) v.e[j] = e[j - 1];
-            if (!(lane == 0 || xb == 0)) {
+            if (!(sub == 0 || xb == 0)) {
                 st_vec<S>(rowp + xb, v);
             } else {
 #pragma unroll
@@ -403,17 +414,17 @@ __device__ __forceinline__ void store_row_shifted_raw(typename Storage<S>::T *ro
 #pragma unroll
             for (int j = 0; j < V; ++j)
                 if (xb + j == nx - 1) rowp[0] = e[j];
-            if (lane == 31 && xb + V < nx) rowp[xb + V] = e[V - 1];
+            if (sub == W - 1 && xb + V < nx) rowp[xb + V] = e[V - 1];
         }
     } else {
-        const T from_right = shfl_down_raw(e[0], 1);
+        const T from_right = shfl_down_raw(e[0], 1, W);
         if (active) {
             Vec<S> v;
 #pragma unroll
             for (int j = 0; j < V - 1; ++j) v.e[j] = e[j + 1];
             v.e[V - 1] = from_right;
             const bool has_row_end = xb + V > nx - 1;
-            const bool last_foreign = (lane == 31) && (xb + V < nx);
+            const bool last_foreign = (sub == W - 1) && (xb + V < nx);
             if (!has_row_end && !last_foreign) {
                 st_vec<S>(rowp + xb, v);
             } else {
@@ -425,7 +436,7 @@ __device__ __forceinline__ void store_row_shifted_raw(typename Storage<S>::T *ro
                 }
             }
             if (xb == 0) rowp[nx - 1] = e[0];
-            else if (lane == 0) rowp[xb - 1] = e[0];
+            else if (sub == 0) rowp[xb - 1] = e[0];
         }
     }
 }

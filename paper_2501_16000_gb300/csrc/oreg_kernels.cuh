@@ -19,39 +19,39 @@ namespace oreg {
 template <int S, int I, bool AA_ODD>
 __device__ __forceinline__ RawRow<S> fetch_plane(const typename Storage<S>::T *base, size_t plane,
                                                  int pitch, int y, int ny, int xb, int nx,
-                                                 int lane) {
+                                                 int sub, int W) {
     // A-B: population i at x comes from plane i at x - c_i.
     // AA odd step: it comes from plane opp(i) at x - c_i (written there by the
     // preceding even step).
     constexpr int P = AA_ODD ? opp_of(I) : I;
     const int ys = wrap_row(y - cy_of(I), ny);
-    return fetch_row<S, cx_of(I), !AA_ODD>(base + P * plane + (size_t)ys * pitch, xb, nx, lane);
+    return fetch_row<S, cx_of(I), !AA_ODD>(base + P * plane + (size_t)ys * pitch, xb, nx, sub, W);
 }
 
 // Gathers the pre-collision populations of the warp's 32*V nodes: all nine
 // row fetches are issued before any is decoded.
 template <int S, bool AA_ODD>
 __device__ __forceinline__ void pull_all(const typename Storage<S>::T *base, size_t plane,
-                                         int pitch, int y, int ny, int xb, int nx, int lane,
+                                         int pitch, int y, int ny, int xb, int nx, int sub, int W,
                                          typename Storage<S>::C f[9][Storage<S>::V]) {
-    const RawRow<S> r0 = fetch_plane<S, 0, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    const RawRow<S> r1 = fetch_plane<S, 1, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    const RawRow<S> r2 = fetch_plane<S, 2, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    const RawRow<S> r3 = fetch_plane<S, 3, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    const RawRow<S> r4 = fetch_plane<S, 4, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    const RawRow<S> r5 = fetch_plane<S, 5, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    const RawRow<S> r6 = fetch_plane<S, 6, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    const RawRow<S> r7 = fetch_plane<S, 7, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    const RawRow<S> r8 = fetch_plane<S, 8, AA_ODD>(base, plane, pitch, y, ny, xb, nx, lane);
-    shift_row<S, cx_of(0)>(r0, xb, nx, lane, f[0]);
-    shift_row<S, cx_of(1)>(r1, xb, nx, lane, f[1]);
-    shift_row<S, cx_of(2)>(r2, xb, nx, lane, f[2]);
-    shift_row<S, cx_of(3)>(r3, xb, nx, lane, f[3]);
-    shift_row<S, cx_of(4)>(r4, xb, nx, lane, f[4]);
-    shift_row<S, cx_of(5)>(r5, xb, nx, lane, f[5]);
-    shift_row<S, cx_of(6)>(r6, xb, nx, lane, f[6]);
-    shift_row<S, cx_of(7)>(r7, xb, nx, lane, f[7]);
-    shift_row<S, cx_of(8)>(r8, xb, nx, lane, f[8]);
+    const RawRow<S> r0 = fetch_plane<S, 0, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    const RawRow<S> r1 = fetch_plane<S, 1, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    const RawRow<S> r2 = fetch_plane<S, 2, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    const RawRow<S> r3 = fetch_plane<S, 3, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    const RawRow<S> r4 = fetch_plane<S, 4, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    const RawRow<S> r5 = fetch_plane<S, 5, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    const RawRow<S> r6 = fetch_plane<S, 6, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    const RawRow<S> r7 = fetch_plane<S, 7, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    const RawRow<S> r8 = fetch_plane<S, 8, AA_ODD>(base, plane, pitch, y, ny, xb, nx, sub, W);
+    shift_row<S, cx_of(0)>(r0, xb, nx, sub, W, f[0]);
+    shift_row<S, cx_of(1)>(r1, xb, nx, sub, W, f[1]);
+    shift_row<S, cx_of(2)>(r2, xb, nx, sub, W, f[2]);
+    shift_row<S, cx_of(3)>(r3, xb, nx, sub, W, f[3]);
+    shift_row<S, cx_of(4)>(r4, xb, nx, sub, W, f[4]);
+    shift_row<S, cx_of(5)>(r5, xb, nx, sub, W, f[5]);
+    shift_row<S, cx_of(6)>(r6, xb, nx, sub, W, f[6]);
+    shift_row<S, cx_of(7)>(r7, xb, nx, sub, W, f[7]);
+    shift_row<S, cx_of(8)>(r8, xb, nx, sub, W, f[8]);
 }
 
 // Row padding (positions nx .. pitch-1 of the last vector of a row) is kept
@@ -110,16 +110,22 @@ __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<
 template <int S, int EQ, int COLL, bool COMP>
 __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict__ src,
                                         typename Storage<S>::T *__restrict__ dst, int nx, int ny,
-                                        int pitch, size_t plane, int y, int seg, int lane,
+                                        int pitch, size_t plane, int y0, int seg, int lane, int lw,
                                         const CollConst<typename Storage<S>::C> &k, long long t,
                                         bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int xb = seg * 32 * V + lane * V;
+    const int W = 1 << lw, sub = lane & (W - 1);
+    int y = y0 + (lane >> lw);
+    int xb = seg * W * V + sub * V;
+    if (y >= ny) {  // rows past the lattice: idle lanes that still shuffle
+        y = ny - 1;
+        xb = nx;
+    }
 
     C f[9][V];
-    pull_all<S, false>(src, plane, pitch, y, ny, xb, nx, lane, f);
+    pull_all<S, false>(src, plane, pitch, y, ny, xb, nx, sub, W, f);
 
     collide_vec<S, EQ, COLL, COMP>(f, k);
 
@@ -142,12 +148,13 @@ template <int S, int EQ, int COLL, bool COMP>
 __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *__restrict__ src,
                                                  typename Storage<S>::T *__restrict__ dst, int nx,
                                                  int ny, int pitch, size_t plane, int segs,
-                                                 const CollConst<typename Storage<S>::C> k,
+                                                 int lw, const CollConst<typename Storage<S>::C> k,
                                                  long long t, bool sr) {
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (item >= (long long)ny * segs) return;  // warp-uniform
-    item_ab<S, EQ, COLL, COMP>(src, dst, nx, ny, pitch, plane, (int)(item / segs),
-                               (int)(item % segs), threadIdx.x & 31, k, t, sr);
+    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
+    if (item >= (long long)groups * segs) return;  // warp-uniform
+    item_ab<S, EQ, COLL, COMP>(src, dst, nx, ny, pitch, plane, (int)(item / segs) << (5 - lw),
+                               (int)(item % segs), threadIdx.x & 31, lw, k, t, sr);
 }
 
 // ---------------------------------------------------------------------------
@@ -158,14 +165,20 @@ __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *_
 // only, so the update is race-free in place.
 // ---------------------------------------------------------------------------
 template <int S, int EQ, int COLL, bool COMP>
-__device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, int pitch,
-                                             size_t plane, int y, int seg, int lane,
+__device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, int ny, int pitch,
+                                             size_t plane, int y0, int seg, int lane, int lw,
                                              const CollConst<typename Storage<S>::C> &k,
                                              long long t, bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int xb = seg * 32 * V + lane * V;
+    const int W = 1 << lw, sub = lane & (W - 1);
+    int y = y0 + (lane >> lw);
+    int xb = seg * W * V + sub * V;
+    if (y >= ny) {  // rows past the lattice: idle lanes that still shuffle
+        y = ny - 1;
+        xb = nx;
+    }
     if (xb >= nx) return;  // no shuffles in the even step
     typename ST::T *row = A + (size_t)y * pitch + xb;
     C f[9][V];
@@ -190,61 +203,69 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
 
 template <int S, int EQ, int COLL, bool COMP>
 __global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A, int nx, int ny,
-                                                      int pitch, size_t plane, int segs,
+                                                      int pitch, size_t plane, int segs, int lw,
                                                       const CollConst<typename Storage<S>::C> k,
                                                       long long t, bool sr) {
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (item >= (long long)ny * segs) return;
-    item_aa_even<S, EQ, COLL, COMP>(A, nx, pitch, plane, (int)(item / segs), (int)(item % segs),
-                                    threadIdx.x & 31, k, t, sr);
+    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
+    if (item >= (long long)groups * segs) return;
+    item_aa_even<S, EQ, COLL, COMP>(A, nx, ny, pitch, plane, (int)(item / segs) << (5 - lw),
+                                    (int)(item % segs), threadIdx.x & 31, lw, k, t, sr);
 }
 
 template <int S, int I>
 __device__ __forceinline__ void push_plane(typename Storage<S>::T *A, size_t plane, int pitch,
-                                           int y, int ny, int xb, int nx, int lane,
+                                           int y, int ny, int xb, int nx, int sub, int W,
                                            const typename Storage<S>::T p[Storage<S>::V]) {
     const int yd = wrap_row(y + cy_of(I), ny);
-    store_row_shifted_raw<S, cx_of(I)>(A + I * plane + (size_t)yd * pitch, xb, nx, lane, p);
+    store_row_shifted_raw<S, cx_of(I)>(A + I * plane + (size_t)yd * pitch, xb, nx, sub, W, p);
 }
 
 template <int S, int EQ, int COLL, bool COMP>
 __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, int ny, int pitch,
-                                            size_t plane, int y, int seg, int lane,
+                                            size_t plane, int y0, int seg, int lane, int lw,
                                             const CollConst<typename Storage<S>::C> &k,
                                             long long t, bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int xb = seg * 32 * V + lane * V;
+    const int W = 1 << lw, sub = lane & (W - 1);
+    int y = y0 + (lane >> lw);
+    int xb = seg * W * V + sub * V;
+    if (y >= ny) {  // rows past the lattice: idle lanes that still shuffle
+        y = ny - 1;
+        xb = nx;
+    }
 
     C f[9][V];
-    pull_all<S, true>(A, plane, pitch, y, ny, xb, nx, lane, f);
+    pull_all<S, true>(A, plane, pitch, y, ny, xb, nx, sub, W, f);
 
     collide_vec<S, EQ, COLL, COMP>(f, k);
     if (xb < nx && xb + V > nx) zero_padding<S>(f, xb, nx);
     typename ST::T e[9][V];
     encode_vec<S>(f, e, xb, y, t, sr);
 
-    push_plane<S, 0>(A, plane, pitch, y, ny, xb, nx, lane, e[0]);
-    push_plane<S, 1>(A, plane, pitch, y, ny, xb, nx, lane, e[1]);
-    push_plane<S, 2>(A, plane, pitch, y, ny, xb, nx, lane, e[2]);
-    push_plane<S, 3>(A, plane, pitch, y, ny, xb, nx, lane, e[3]);
-    push_plane<S, 4>(A, plane, pitch, y, ny, xb, nx, lane, e[4]);
-    push_plane<S, 5>(A, plane, pitch, y, ny, xb, nx, lane, e[5]);
-    push_plane<S, 6>(A, plane, pitch, y, ny, xb, nx, lane, e[6]);
-    push_plane<S, 7>(A, plane, pitch, y, ny, xb, nx, lane, e[7]);
-    push_plane<S, 8>(A, plane, pitch, y, ny, xb, nx, lane, e[8]);
+    push_plane<S, 0>(A, plane, pitch, y, ny, xb, nx, sub, W, e[0]);
+    push_plane<S, 1>(A, plane, pitch, y, ny, xb, nx, sub, W, e[1]);
+    push_plane<S, 2>(A, plane, pitch, y, ny, xb, nx, sub, W, e[2]);
+    push_plane<S, 3>(A, plane, pitch, y, ny, xb, nx, sub, W, e[3]);
+    push_plane<S, 4>(A, plane, pitch, y, ny, xb, nx, sub, W, e[4]);
+    push_plane<S, 5>(A, plane, pitch, y, ny, xb, nx, sub, W, e[5]);
+    push_plane<S, 6>(A, plane, pitch, y, ny, xb, nx, sub, W, e[6]);
+    push_plane<S, 7>(A, plane, pitch, y, ny, xb, nx, sub, W, e[7]);
+    push_plane<S, 8>(A, plane, pitch, y, ny, xb, nx, sub, W, e[8]);
 }
 
 template <int S, int EQ, int COLL, bool COMP>
 __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
-                                                     int pitch, size_t plane, int segs,
+                                                     int pitch, size_t plane, int segs, int lw,
                                                      const CollConst<typename Storage<S>::C> k,
                                                      long long t, bool sr) {
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (item >= (long long)ny * segs) return;
-    item_aa_odd<S, EQ, COLL, COMP>(A, nx, ny, pitch, plane, (int)(item / segs), (int)(item % segs),
-                                   threadIdx.x & 31, k, t, sr);
+    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
+    if (item >= (long long)groups * segs) return;
+    item_aa_odd<S, EQ, COLL, COMP>(A, nx, ny, pitch, plane, (int)(item / segs) << (5 - lw),
+                                   (int)(item % segs), threadIdx.x & 31, lw, k, t, sr);
 }
 
 // ---------------------------------------------------------------------------
@@ -262,13 +283,15 @@ template <int S> struct StepLaunch {
         if (a.layout == 0) {
             k_step_ab<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
                 static_cast<const T *>(a.src), static_cast<T *>(a.dst), a.nx, a.ny, a.pitch,
-                a.plane, segs, k, a.t, a.sr != 0);
+                a.plane, segs, a.lw, k, a.t, a.sr != 0);
         } else if (a.parity == 0) {
             k_step_aa_even<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
-                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, k, a.t, a.sr != 0);
+                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
+                a.sr != 0);
         } else {
             k_step_aa_odd<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
-                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, k, a.t, a.sr != 0);
+                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
+                a.sr != 0);
         }
     }
 
@@ -285,7 +308,8 @@ template <int S> struct StepLaunch {
 
     static cudaError_t step(const StepArgs &a) {
         const int warps = a.warps_per_block;
-        const long long items = (long long)a.ny * a.segs;
+        const long long groups = (a.ny + (32 >> a.lw) - 1) >> (5 - a.lw);
+        const long long items = groups * a.segs;
         dim3 block(32 * warps);
         dim3 grid((unsigned)((items + warps - 1) / warps));
         if (a.comp && S == ST_F32) step_comp<true>(a, grid, block);

@@ -26,7 +26,8 @@ struct StepArgs {
     void *dst;         // A-B: buffer of S_{t+1}; AA: unused
     int nx, ny, pitch;
     size_t plane;
-    int segs;          // row segments of 32*V nodes per row
+    int segs;          // row segments of W*V nodes per row
+    int lw;            // log2 of W, the lanes per row segment (W <= 32)
     int eq, coll, layout, parity;
     int comp;          // compensated conserved-moment sums (FP32 only)
     int sr;            // stochastic rounding (half formats only)
@@ -35,6 +36,15 @@ struct StepArgs {
     const void *kconst;  // CollConst<C> of the storage's compute type
     cudaStream_t stream;
 };
+
+// Lanes per row segment for a lattice nx wide: the smallest power of two
+// W <= 32 whose segment (W vectors of V elements) covers the row, as log2.
+inline int segment_log2(int nx, int V) {
+    const int vecs = (nx + V - 1) / V;
+    int lw = 0;
+    while (lw < 5 && (1 << lw) < vecs) ++lw;
+    return lw;
+}
 
 enum { INIT_SHEAR = 0, INIT_SHOCK = 1, INIT_FIELDS = 2 };
 
@@ -80,8 +90,8 @@ OREG_DECLARE_LAUNCHERS(bf16)
 // One launch of the batched stream-collide kernel (see oreg_batch_kernels.cuh).
 struct BatchLaunch {
     const void *descs;        // BatchDesc<C>[]
-    const int4 *items;        // work items (descriptor, row, segment)
-    const int *n_items;       // device: number of valid items
+    const int4 *items;        // work items (descriptor, first row, segment), grouped
+    const int *groups;        // device: item offsets of the 8 groups (9 entries)
     const long long *g;       // device: global step counter of this round
     int k;                    // step within the round
     int layout;

@@ -126,17 +126,17 @@ __global__ void __launch_bounds__(NOALLOC_THREADS)
 CollConst<double> noalloc_constants(const olb_params *p) {
     CollConst<double> k{};
     const double th = p->eq == OLB_EQ_GUIDED ? p->theta : 1.0 / 3.0;
-    const double psi0[3] = {1.0 - th, 0.5 * th, 0.5 * th};
-    for (int a = 0; a < 3; ++a) k.psi0[a] = psi0[a];
+    const double psi0[2] = {1.0 - th, 0.5 * th};
+    for (int a = 0; a < 2; ++a) k.psi0[a] = psi0[a];
+    const double w[3] = {psi0[0] * psi0[0], psi0[0] * psi0[1], psi0[1] * psi0[1]};
+    const int count[3] = {1, 4, 4};
     double corr_sum = 0.0;
-    for (int i = 0; i < 9; ++i) {
-        const double w = psi0[kidx(cx_of(i))] * psi0[kidx(cy_of(i))];
-        const double s = p->storage == OLB_F64 ? w * p->rho0 : (double)(float)(w * p->rho0);
-        k.w[i] = w;
-        k.w_lo[i] = 0.0;
-        k.shift[i] = s;
-        k.corr[i] = w * p->rho0 - s;
-        corr_sum += k.corr[i];
+    for (int c = 0; c < 3; ++c) {
+        const double s = p->storage == OLB_F64 ? w[c] * p->rho0 : (double)(float)(w[c] * p->rho0);
+        k.w[c] = w[c];
+        k.shift[c] = s;
+        k.corr[c] = w[c] * p->rho0 - s;
+        corr_sum += count[c] * k.corr[c];
     }
     k.sum_corr = corr_sum;
     k.rho0 = p->rho0;
