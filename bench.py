@@ -148,6 +148,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value: float, device="cpu") -> float:
+    """Maximum of a per-rank value over all ranks (identity without a process
+    group); the only collective the benchmark uses (timing, not data)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_mlups(world: int, nodes_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank advances its own lattice of
+    nodes_per_rank nodes `steps` times; the slowest rank sets the time."""
+    return world * nodes_per_rank * steps / (max_ms / 1e3) / 1e6
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -290,11 +308,8 @@ def run_native(args):
     clocks = sampler.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
     kern_ms = sum(a.elapsed_time(b) for a, b in ev) / K
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    mlups = world * N * K / (elapsed_ms / 1e3) / 1e6
+    elapsed_ms = max_over_ranks(elapsed_ms, "cuda")
+    mlups = weak_scaling_mlups(world, N, K, elapsed_ms)
 
     bpn = bytes_per_node_step(args.storage)
     peak, peak_kind = measured_peaks()
@@ -320,10 +335,7 @@ def run_native(args):
             for a in h[3:6]], None)
         barrier()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, "cuda")
         e2e = {"value": round(world * N * K / e2e_s / 1e6, 1), "unit": "MLUPS",
                "h2d_bytes_per_step": int(3 * N * 8 / K), "d2h_bytes_per_step": int(3 * N * 8 / K),
                "note": f"one solve of {K} steps: olb_init_fields from pinned host fields, "

@@ -58,6 +58,17 @@ def shear_wave_fields(nx, ny, rho0, u0, m, n):
     return rho, u0 * ex * s, u0 * ey * s
 
 
+def shear_wave_window(nx, ny, rho0, u0, m, n, x0, y0, wx, wy):
+    """(rho, ux, uy) of the nx x ny shear wave on the window of wx x wy nodes
+    whose first node is the global node (x0, y0) (coordinates wrap)."""
+    x = (x0 + np.arange(wx, dtype=np.int64))[None, :] % nx
+    y = (y0 + np.arange(wy, dtype=np.int64))[:, None] % ny
+    num = np.mod(m * x * ny + n * y * nx, nx * ny)
+    s = np.sin(2.0 * np.pi * (num.astype(np.float64) / float(nx * ny)))
+    ex, ey = shear_wave_direction(nx, ny, m, n)
+    return np.full((wy, wx), float(rho0)), u0 * ex * s, u0 * ey * s
+
+
 def shock_tube_fields(nx, ny, rho_left, rho_right, x_split):
     """(rho, ux, uy) of the isothermal shock tube, a density step at x_split."""
     x = np.arange(nx)[None, :]

@@ -1,0 +1,79 @@
+"""The 8192 x 8192 rotated shear wave (benchmark lattice) on the GPU.
+
+FP64 GPU vs the FP64 oracle through a domain-of-dependence crop: after T
+steps a node depends only on initial nodes within Chebyshev distance T, so
+the oracle runs a (W + 2T)^2 window initialised from the same global field
+(periodic on the window: the wrap contaminates only the outer T nodes) and
+its central W x W block must equal the GPU crop.  The FP32, FP16 and BF16
+runs are compared with the FP64 GPU run on windows across the lattice."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_16000_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_16000_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("theta", [1.0 / 3.0, 0.3])
+def test_8192_fp64_crop_matches_oracle(theta):
+    from paper_2501_16000_gb300.engine import Lattice
+    case = W.large_shear(theta=theta, seed=0, side=8192, steps=200)
+    T, Wd = case.steps, 256
+    crops = [(4000, 4000), (8192 - 128, 8192 - 100)]       # interior and across the wrap
+    with Lattice(case.nx, case.ny, case.tau, theta, storage="f64", layout="aa") as lat:
+        lat.init_case(case)
+        lat.step(T)
+        got = {c: lat.region(c[0] % 8192, c[1] % 8192, Wd, Wd)
+               for c in crops if c[0] + Wd <= 8192 and c[1] + Wd <= 8192}
+        # a crop straddling the periodic boundary is read in pieces
+        x0, y0 = crops[1]
+        big = np.empty((9, Wd, Wd))
+        for (xs, wx, gx) in ((x0, 8192 - x0, 0), (0, Wd - (8192 - x0), 8192 - x0)):
+            for (ys, wy, gy) in ((y0, 8192 - y0, 0), (0, Wd - (8192 - y0), 8192 - y0)):
+                big[:, gy:gy + wy, gx:gx + wx] = lat.region(xs, ys, wx, wy)
+        got[crops[1]] = big
+    p = O.params(Wd + 2 * T, Wd + 2 * T, case.tau, theta, O.GUIDED, O.OREG)
+    for (x0, y0), g in got.items():
+        fields = W.shear_wave_window(case.nx, case.ny, 1.0, case.u0, case.m, case.n,
+                                     x0 - T, y0 - T, Wd + 2 * T, Wd + 2 * T)
+        ref = O.run(O.init_equilibrium(p, *fields), p, T)[:, T:T + Wd, T:T + Wd]
+        err = np.abs(g - ref).max() / np.abs(ref).max()
+        assert err <= 1e-12, ((x0, y0), err)
+
+
+def test_8192_reduced_precision_vs_fp64():
+    from paper_2501_16000_gb300.engine import Lattice
+    case = W.large_shear(theta=1.0 / 3.0, seed=0, side=8192, steps=500)
+    wins = [(0, 0), (4096, 1024), (8192 - 256, 8192 - 256)]
+    res = {}
+    for st in ("f64", "f32", "f16", "bf16"):
+        with Lattice(case.nx, case.ny, case.tau, storage=st, layout="ab") as lat:
+            lat.init_case(case)
+            lat.step(case.steps)
+            res[st] = [lat.region(x, y, 256, 256) for x, y in wins]
+            if st == "f64":
+                d64 = lat.diagnostics()
+            else:
+                d = lat.diagnostics()
+                drift = abs(d["mass"] / d64["mass"] - 1)
+                print(st, "relative mass difference to FP64 after 500 steps:", drift)
+                # FP32 arithmetic drifts ~1e-11 per step; stochastic half-format
+                # rounding adds unbiased noise of ~1e-3 ulp-relative per node
+                assert drift < {"f32": 1e-7, "f16": 1e-5, "bf16": 1e-4}[st]
+    den = max(np.abs(r).max() for r in res["f64"])
+    err = {st: max(np.abs(a - b).max() for a, b in zip(res[st], res["f64"])) / den
+           for st in ("f32", "f16", "bf16")}
+    print("8192^2, 500 steps, rel Linf vs FP64 GPU:", err)
+    assert err["f32"] <= 1e-5
+    assert err["f16"] <= 1e-3
+    assert err["bf16"] <= 1e-2
