@@ -150,6 +150,59 @@ template <typename C> struct CollConst {
     C theta;         // lattice theta (guided) or theta0 (poly2)
 };
 
+// ---------------------------------------------------------------------------
+// Two FP32 lanes in one 64-bit register pair, computed with the packed
+// add/sub/mul/fma.rn.f32x2 instructions of sm_100-class GPUs: each lane is
+// rounded exactly as the scalar FP32 operation would round it.  The half
+// storage formats collide two nodes per instruction this way.
+// ---------------------------------------------------------------------------
+struct F2 {
+    unsigned long long v;
+    __device__ __forceinline__ F2() : v(0ull) {}
+    __device__ __forceinline__ explicit F2(unsigned long long r) : v(r) {}
+    __device__ __forceinline__ F2(float a, float b) {
+        asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(a), "f"(b));
+    }
+    __device__ __forceinline__ explicit F2(float a) {  // broadcast
+        asm("mov.b64 %0, {%1, %1};" : "=l"(v) : "f"(a));
+    }
+    __device__ __forceinline__ explicit F2(int a) : F2((float)a) {}
+    __device__ __forceinline__ explicit F2(double a) : F2((float)a) {}
+    __device__ __forceinline__ float lo() const {
+        float a, b;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+        return a;
+    }
+    __device__ __forceinline__ float hi() const {
+        float a, b;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+        return b;
+    }
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(0.0f) - a; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2(a.lo() / b.lo(), a.hi() / b.hi()); }
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+using ::fma;  // keep the scalar overloads visible next to the packed one
+
 // Error-free sum: a + b = s + e exactly (Knuth TwoSum).
 template <typename C>
 __device__ __forceinline__ void two_sum(C a, C b, C &s, C &e) {

@@ -91,18 +91,59 @@ __device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Sto
         for (int j = 0; j < ST::V; ++j) e[i][j] = ST::enc(f[i][j]);
 }
 
+// The collision constants broadcast to both lanes of a packed pair.
+__device__ __forceinline__ CollConst<F2> broadcast(const CollConst<float> &k) {
+    CollConst<F2> b;
+    b.rho0 = F2(k.rho0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        b.psi0[a] = F2(k.psi0[a]);
+        b.psi0_lo[a] = F2(k.psi0_lo[a]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        b.w[c] = F2(k.w[c]);
+        b.w_lo[c] = F2(k.w_lo[c]);
+        b.shift[c] = F2(k.shift[c]);
+        b.corr[c] = F2(k.corr[c]);
+    }
+    b.sum_corr = F2(k.sum_corr);
+    b.lam = F2(k.lam);
+    b.inv_2th2 = F2(k.inv_2th2);
+    b.theta = F2(k.theta);
+    return b;
+}
+
+// Collides the V nodes of a lane.  The half formats (V = 8, FP32 compute)
+// collide node pairs with packed f32x2 arithmetic.
 template <int S, int EQ, int COLL, bool COMP>
 __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<S>::V],
                                             const CollConst<typename Storage<S>::C> &k) {
     using C = typename Storage<S>::C;
+    if constexpr ((S == ST_F16 || S == ST_BF16) && !COMP) {
+        const CollConst<F2> k2 = broadcast(k);
 #pragma unroll
-    for (int j = 0; j < Storage<S>::V; ++j) {
-        C g[9], post[9];
+        for (int j = 0; j < Storage<S>::V; j += 2) {
+            F2 g[9], post[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = f[i][j];
-        collide<EQ, COLL, C, COMP>(g, post, k);
+            for (int i = 0; i < 9; ++i) g[i] = F2(f[i][j], f[i][j + 1]);
+            collide<EQ, COLL, F2, false>(g, post, k2);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i][j] = post[i];
+            for (int i = 0; i < 9; ++i) {
+                f[i][j] = post[i].lo();
+                f[i][j + 1] = post[i].hi();
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < Storage<S>::V; ++j) {
+            C g[9], post[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = f[i][j];
+            collide<EQ, COLL, C, COMP>(g, post, k);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i][j] = post[i];
+        }
     }
 }
 
