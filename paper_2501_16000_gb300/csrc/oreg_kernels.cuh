@@ -114,8 +114,10 @@ __device__ __forceinline__ CollConst<F2> broadcast(const CollConst<float> &k) {
     return b;
 }
 
-// Collides the V nodes of a lane.  The half formats (V = 8, FP32 compute)
-// collide node pairs with packed f32x2 arithmetic.
+// Collides the V nodes of a lane.  The half formats (V = 8, FP32 compute,
+// issue-bound) collide node pairs with packed f32x2 arithmetic; FP32 storage
+// (HBM-bound) stays scalar, where packing measured no faster for A-B and
+// slower for AA.
 template <int S, int EQ, int COLL, bool COMP>
 __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<S>::V],
                                             const CollConst<typename Storage<S>::C> &k) {
