@@ -65,13 +65,16 @@ def _bytes(lat_case, storage, layout):
 class Server:
     def __init__(self, storage="f16", layout="ab", budget_bytes=120e9, steps_per_launch=100,
                  max_lattices=8192, max_items=1 << 24, warps_per_block=4, blocks_per_sm=0,
-                 keep_fields=True):
+                 keep_fields=True, engine=None):
+        """``engine`` replaces the BatchEngine (anything with its new_lattice,
+        add, remove, remaining, run, wait and close methods)."""
         self.storage, self.layout = storage, layout
         self.budget = float(budget_bytes)
         self.keep_fields = keep_fields
-        self.engine = BatchEngine(storage, layout, max_lattices=max_lattices,
-                                  max_items=max_items, steps_per_launch=steps_per_launch,
-                                  warps_per_block=warps_per_block, blocks_per_sm=blocks_per_sm)
+        self.engine = engine if engine is not None else BatchEngine(
+            storage, layout, max_lattices=max_lattices, max_items=max_items,
+            steps_per_launch=steps_per_launch, warps_per_block=warps_per_block,
+            blocks_per_sm=blocks_per_sm)
         self.max_items = max_items
         self.rounds = 0
         self.peak_bytes = 0

@@ -1,0 +1,130 @@
+"""Host-side logic on CPU: seeded input generators, the decay-rate fit, the
+work-item count and the serving loop's admission against a memory budget
+(with a stand-in for the GPU batch engine)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2501_16000_gb300 import workloads as W
+from paper_2501_16000_gb300.analysis import fit_decay
+from paper_2501_16000_gb300.batch import work_items
+from paper_2501_16000_gb300.engine import required_bytes
+
+
+def test_generators_are_seeded_and_in_range():
+    a, b = W.batch_mix(64, seed=1), W.batch_mix(64, seed=1)
+    assert a == b
+    assert a != W.batch_mix(64, seed=2)
+    for c in a:
+        assert 32 <= c.nx <= 1024 and 32 <= c.ny <= 1024
+        assert 0.51 <= c.tau <= 1.0
+        if c.case == "shear":
+            assert (c.m, c.n) != (0, 0) and 0.01 <= c.u0 <= 0.1
+        else:
+            assert c.x_split == c.nx // 2
+    t = W.arrival_trace(100, rate_per_s=10.0, seed=2)
+    arr = [r.arrival_s for r in t]
+    assert arr == sorted(arr) and all(64 <= r.lattice.nx <= 2048 for r in t)
+    assert all(100 <= r.lattice.steps <= 10000 for r in t)
+    # mean inter-arrival of a Poisson process
+    assert 0.05 < np.mean(np.diff([0.0] + arr)) < 0.2
+
+
+def test_shear_wave_fields_and_window_agree():
+    rho, ux, uy = W.shear_wave_fields(40, 30, 1.0, 0.05, 3, 2)
+    ex, ey = W.shear_wave_direction(40, 30, 3, 2)
+    assert np.allclose(ux * ey - uy * ex, 0.0)                 # velocity along e_perp
+    assert abs(np.sum(ux)) < 1e-12 and np.isclose(np.abs(ux * ex + uy * ey).max(), 0.05, atol=2e-3)
+    wr, wx, wy = W.shear_wave_window(40, 30, 1.0, 0.05, 3, 2, 35, 25, 10, 10)   # wraps
+    xs, ys = (35 + np.arange(10)) % 40, (25 + np.arange(10)) % 30
+    assert np.array_equal(wx, ux[np.ix_(ys, xs)]) and np.array_equal(wy, uy[np.ix_(ys, xs)])
+    m, n, ang = W.wave_vector_from_angle(8192, 8192, math.pi / 6)
+    assert (m, n) == (111, 64) and abs(ang - math.pi / 6) < 1e-2
+
+
+def test_fit_decay_recovers_an_exponential():
+    ts = np.arange(0, 2001, 20, dtype=float)
+    amps = 0.05 * np.exp(-3e-3 * ts)
+    assert abs(fit_decay(ts, amps, tau=0.8) / 3e-3 - 1) < 1e-12
+    noisy = amps * (1 + 1e-6 * np.random.default_rng(0).standard_normal(ts.size))
+    noisy[ts > 1000] = 1e-9                                    # noise floor: excluded
+    assert abs(fit_decay(ts, noisy, tau=0.8) / 3e-3 - 1) < 1e-3
+    with pytest.raises(ValueError):
+        fit_decay([0, 10], [1.0, 0.9], tau=0.8)
+
+
+@pytest.mark.parametrize("storage,v", [("f64", 2), ("f32", 4), ("f16", 8)])
+def test_work_items_cover_every_node_once(storage, v):
+    for nx in (1, 5, 37, 100, 256, 257, 1024, 3000):
+        for ny in (1, 3, 32, 33):
+            vecs = math.ceil(nx / v)
+            w = 1
+            while w < 32 and w < vecs:
+                w *= 2
+            assert work_items(nx, ny, storage) * 32 * v >= nx * ny
+            assert work_items(nx, ny, storage) == math.ceil(ny / (32 // w)) * math.ceil(nx / (w * v))
+
+
+class _FakeLattice:
+    def __init__(self, case):
+        self.case, self.closed = case, False
+
+    def moments(self):
+        return (np.ones((self.case.ny, self.case.nx)),) * 3
+
+    def close(self):
+        self.closed = True
+
+
+class _FakeEngine:
+    """Advances every member K steps per round; no GPU."""
+
+    def __init__(self, K):
+        self.K, self.left, self.order, self.rounds = K, {}, [], 0
+
+    def new_lattice(self, case):
+        return _FakeLattice(case)
+
+    def add(self, lat, n):
+        self.left[id(lat)] = n
+        self.order.append(lat.case)
+
+    def remove(self, lat):
+        del self.left[id(lat)]
+
+    def remaining(self, lat):
+        return self.left[id(lat)]
+
+    def run(self, n=1):
+        self.rounds += n
+        for k in self.left:
+            self.left[k] = max(0, self.left[k] - n * self.K)
+
+    def wait(self):
+        pass
+
+    def close(self):
+        pass
+
+
+def test_serving_admission_fifo_and_budget():
+    from paper_2501_16000_gb300 import build
+    build.build()                                   # required_bytes is a host-only library call
+    from paper_2501_16000_gb300.serve import Server
+    trace = W.arrival_trace(30, rate_per_s=2000.0, seed=5, lo=16, hi=256, steps_lo=10,
+                            steps_hi=500)
+    sizes = [required_bytes(nx=r.lattice.nx, ny=r.lattice.ny, tau=r.lattice.tau,
+                            storage="f16", layout="ab") for r in trace]
+    budget = 3 * max(sizes)
+    eng = _FakeEngine(K=50)
+    srv = Server("f16", "ab", budget_bytes=budget, engine=eng)
+    results, wall = srv.run(trace)
+    assert len(results) == len(trace)
+    assert srv.peak_bytes <= budget and srv.peak_inflight >= 2
+    # admission is first come, first served
+    assert [c for c in eng.order] == [r.lattice for r in sorted(trace, key=lambda r: r.arrival_s)]
+    for r in results:
+        assert r.done_s >= r.admitted_s >= r.arrival_s - 1e-9 and r.latency_s >= 0
+        assert r.fields[0].shape == (next(q.lattice.ny for q in trace if q.rid == r.rid),
+                                     next(q.lattice.nx for q in trace if q.rid == r.rid))
