@@ -10,7 +10,8 @@ Each call restates one passage of arXiv 2501.16000:
   foreg        Eq. 6
   collide      Eq. 7 (OReg) or Eq. 1 (BGK), one node
   stream       streaming of Eqs. 1/7 (x -> x + c_i, periodic)
-  step / run   collide + stream at every node
+  step / run   collide (or bounce back at wall nodes) + stream at every node
+  first_order  Eq. 5, one node; init_first_order: S_0 = f^eq + f^(1)
   fields       rho, u and the local temperature of Eq. 2a
 """
 from __future__ import annotations
@@ -38,7 +39,8 @@ _lib = None
 class OraParams(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("theta", ctypes.c_double),
-                ("eq", ctypes.c_int32), ("coll", ctypes.c_int32)]
+                ("eq", ctypes.c_int32), ("coll", ctypes.c_int32),
+                ("walls", ctypes.c_int32)]
 
 
 def build(force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:
@@ -76,10 +78,14 @@ def load(path: str) -> ctypes.CDLL:
     L.ora_foreg.argtypes = [d, d, ctypes.c_double, ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, d]
     L.ora_collide_node.argtypes = [P, d, d]
+    L.ora_bounce_back_node.argtypes = [d, d]
     L.ora_stream.argtypes = [ctypes.c_int32, ctypes.c_int32, d, d]
     L.ora_step.argtypes = [P, d, d]
     L.ora_run.argtypes = [P, d, d, ctypes.c_int64]
     L.ora_init_equilibrium.argtypes = [P, d, d, d, d]
+    L.ora_first_order.argtypes = [ctypes.c_double, ctypes.c_double, d, ctypes.c_double,
+                                  ctypes.c_double, d, d]
+    L.ora_init_first_order.argtypes = [P, d, d, d, d, d]
     L.ora_fields.argtypes = [ctypes.c_int32, ctypes.c_int32, d, d, d, d, d]
     L.ora_velocities.argtypes = [ctypes.POINTER(ctypes.c_int32)]
     L.ora_set_threads.argtypes = [ctypes.c_int]
@@ -133,8 +139,10 @@ def get_threads() -> int:
     return int(lib().ora_get_threads())
 
 
-def params(nx, ny, tau, theta=1.0 / 3.0, eq=GUIDED, coll=OREG) -> OraParams:
-    return OraParams(int(nx), int(ny), float(tau), float(theta), int(eq), int(coll))
+def params(nx, ny, tau, theta=1.0 / 3.0, eq=GUIDED, coll=OREG, walls=False) -> OraParams:
+    """walls: columns x = 0 and nx - 1 are full-way bounce-back walls."""
+    return OraParams(int(nx), int(ny), float(tau), float(theta), int(eq), int(coll),
+                     1 if walls else 0)
 
 
 def feq(eq: int, theta: float, rho: float, ux: float, uy: float) -> np.ndarray:
@@ -201,6 +209,27 @@ def init_equilibrium(p: OraParams, rho, ux, uy) -> np.ndarray:
     assert rho.shape == (p.ny, p.nx)
     f = np.empty((9, p.ny, p.nx))
     lib().ora_init_equilibrium(ctypes.byref(p), _p(rho), _p(ux), _p(uy), _p(f))
+    return f
+
+
+def first_order(tau: float, eq: int, theta: float, rho: float, ux: float, uy: float,
+                grad) -> np.ndarray:
+    """Eq. 5 for one node; grad[a][b] = d_b u_a."""
+    g = _f64(grad).reshape(4)
+    fe = feq(eq, theta, rho, ux, uy)
+    theta_eff = theta if eq == GUIDED else 1.0 / 3.0
+    out = np.zeros(9)
+    lib().ora_first_order(float(tau), float(theta_eff), _p(fe), float(ux), float(uy), _p(g),
+                          _p(out))
+    return out
+
+
+def init_first_order(p: OraParams, rho, ux, uy, grad) -> np.ndarray:
+    """S_0 = f^eq + f^(1) (Eq. 5); grad has shape (2, 2, ny, nx), grad[a, b] = d_b u_a."""
+    rho, ux, uy, grad = _f64(rho), _f64(ux), _f64(uy), _f64(grad)
+    assert rho.shape == (p.ny, p.nx) and grad.shape == (2, 2, p.ny, p.nx)
+    f = np.empty((9, p.ny, p.nx))
+    lib().ora_init_first_order(ctypes.byref(p), _p(rho), _p(ux), _p(uy), _p(grad), _p(f))
     return f
 
 

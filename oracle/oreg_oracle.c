@@ -21,6 +21,11 @@
  *   ora_stream         left-hand side of Eqs. 1 and 7: the post-collision
  *                      population i at x lands at x + c_i (periodic).
  *   ora_step           one full time step = collide at every node, then stream.
+ *   ora_bounce_back_node  full-way bounce-back at the wall nodes of the Sec. IV
+ *                      shock tube (post_i = f_opp(i)).
+ *   ora_first_order    Eq. 5 (first-order populations from a velocity
+ *                      gradient), used to start a run without the transient
+ *                      of an equilibrium start.
  *
  * Parity status: pinned by the closed forms of Eqs. 2, 12, 13, 16 and 17, by
  * streaming translation, conservation, the viscous shear-wave decay of
@@ -49,6 +54,8 @@ typedef struct {
     double theta;     /* lattice temperature used by the guided equilibrium */
     int32_t eq;       /* 0 = guided (Eq. 11), 1 = polynomial (Eq. 15) */
     int32_t coll;     /* 0 = OReg (Eq. 7), 1 = BGK (Eq. 1) */
+    int32_t walls;    /* 1: columns x = 0 and x = nx - 1 are full-way
+                         bounce-back walls (Sec. IV shock tube); 0: periodic */
 } ora_params;
 
 /* Reference temperature of the polynomial equilibrium (Eq. 15). */
@@ -189,6 +196,17 @@ void ora_collide_node(const ora_params *p, const double *f, double *post) {
     }
 }
 
+/* Full-way bounce-back at a solid wall node (Sec. IV shock tube): the node
+ * does not collide; each population arriving along c_i leaves along -c_i,
+ * post_i = f_k with c_k = -c_i. */
+void ora_bounce_back_node(const double *f, double *post) {
+    for (int i = 0; i < ORA_Q; ++i) {
+        for (int k = 0; k < ORA_Q; ++k) {
+            if (ORA_C[k][0] == -ORA_C[i][0] && ORA_C[k][1] == -ORA_C[i][1]) post[i] = f[k];
+        }
+    }
+}
+
 static int64_t ora_wrap(int64_t v, int64_t n) {
     int64_t r = v % n;
     return r < 0 ? r + n : r;
@@ -209,8 +227,10 @@ void ora_stream(int32_t nx, int32_t ny, const double *post, double *dst) {
     }
 }
 
-/* One time step S_t -> S_{t+1}: collide at every node, then push each
- * post-collision population to its neighbour.  src and dst must not alias.
+/* One time step S_t -> S_{t+1}: collide at every node (bounce back at wall
+ * nodes), then push each post-collision population to its neighbour; the
+ * push wraps periodically in both axes (with walls, what crosses between the
+ * two wall columns stays inside the walls).  src and dst must not alias.
  * Rows are independent, so they may run on several host threads without
  * changing any result. */
 void ora_step(const ora_params *p, const double *src, double *dst) {
@@ -220,7 +240,10 @@ void ora_step(const ora_params *p, const double *src, double *dst) {
         for (int64_t x = 0; x < nx; ++x) {
             double f[ORA_Q], post[ORA_Q];
             for (int i = 0; i < ORA_Q; ++i) f[i] = src[i * N + y * nx + x];
-            ora_collide_node(p, f, post);
+            if (p->walls && (x == 0 || x == nx - 1))
+                ora_bounce_back_node(f, post);
+            else
+                ora_collide_node(p, f, post);
             for (int i = 0; i < ORA_Q; ++i) {
                 const int64_t yd = ora_wrap(y + ORA_C[i][1], ny);
                 const int64_t xd = ora_wrap(x + ORA_C[i][0], nx);
@@ -252,6 +275,47 @@ void ora_init_equilibrium(const ora_params *p, const double *rho, const double *
         double feq[ORA_Q];
         ora_feq(p->eq, p->theta, rho[n], ux[n], uy[n], feq);
         for (int i = 0; i < ORA_Q; ++i) f[i * N + n] = feq[i];
+    }
+}
+
+/* Eq. 5: the Navier-Stokes-level populations of Eq. 4 projected on the
+ * lattice,
+ *   f_i^(1) = -tau f_i^eq sum_{a,b} (C_ia C_ib - C_i^2 delta_ab / D)
+ *                                  * (d_b u_a + d_a u_b) / (2 theta),
+ * with C_i = c_i - u and the velocity gradient grad[a][b] = d_b u_a of one
+ * node.  theta_eff is the temperature of Eq. 6 (ora_theta_eff). */
+void ora_first_order(double tau, double theta_eff, const double *feq, double ux, double uy,
+                     const double *grad /* [2][2] */, double *f1 /* [9] */) {
+    const double u[ORA_D] = {ux, uy};
+    for (int i = 0; i < ORA_Q; ++i) {
+        double Cp[ORA_D]; /* peculiar velocity C_i */
+        for (int a = 0; a < ORA_D; ++a) Cp[a] = (double)ORA_C[i][a] - u[a];
+        const double Cp2 = Cp[0] * Cp[0] + Cp[1] * Cp[1];
+        double contraction = 0.0;
+        for (int a = 0; a < ORA_D; ++a) {
+            for (int b = 0; b < ORA_D; ++b) {
+                const double delta = (a == b) ? 1.0 : 0.0;
+                const double rate = (grad[a * ORA_D + b] + grad[b * ORA_D + a]) / (2.0 * theta_eff);
+                contraction += (Cp[a] * Cp[b] - Cp2 * delta / (double)ORA_D) * rate;
+            }
+        }
+        f1[i] = -tau * feq[i] * contraction;
+    }
+}
+
+/* S_0 = f^eq + f^(1) (Eq. 5) at every node, from the density, velocity and
+ * velocity-gradient fields; grad holds d_b u_a at grad[(a*2 + b)*N + n]. */
+void ora_init_first_order(const ora_params *p, const double *rho, const double *ux,
+                          const double *uy, const double *grad, double *f) {
+    const int64_t N = (int64_t)p->nx * p->ny;
+    const double theta_eff = ora_theta_eff(p->eq, p->theta);
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        double feq[ORA_Q], f1[ORA_Q], g[ORA_D * ORA_D];
+        for (int ab = 0; ab < ORA_D * ORA_D; ++ab) g[ab] = grad[ab * N + n];
+        ora_feq(p->eq, p->theta, rho[n], ux[n], uy[n], feq);
+        ora_first_order(p->tau, theta_eff, feq, ux[n], uy[n], g, f1);
+        for (int i = 0; i < ORA_Q; ++i) f[i * N + n] = feq[i] + f1[i];
     }
 }
 

@@ -8,8 +8,10 @@ streaming), so both the CUDA path's tests and the CPU oracle's tests may use it.
 Initial conditions:
   * rotated decaying shear wave (Sec. IV, Eq. 18 generalised to any integer
     wave vector on a periodic lattice):
-      k = 2 pi (m / nx, n / ny),  u(x) = u0 sin(k . x) e_perp,
-      e_perp = (-k_y, k_x) / |k|,  rho = rho0, no mean flow;
+      k = 2 pi (m / nx, n / ny),  u(x) = U + u0 sin(k . x) e_perp,
+      e_perp = (-k_y, k_x) / |k|,  rho = rho0, U a uniform mean flow (zero
+    except in the Mach sweep of Fig. 2), and its analytic velocity gradient
+    for the first-order start of Eq. 5;
   * isothermal shock tube (Sec. IV): rho = rho_left for x < x_split,
     rho_right otherwise, u = 0, periodic in both axes.
 """
@@ -49,13 +51,24 @@ def wave_number_sq(nx: int, ny: int, m: int, n: int) -> float:
     return (2.0 * math.pi) ** 2 * ((m / nx) ** 2 + (n / ny) ** 2)
 
 
-def shear_wave_fields(nx, ny, rho0, u0, m, n):
-    """(rho, ux, uy) float64 arrays (ny, nx) of the rotated shear wave."""
+def shear_wave_fields(nx, ny, rho0, u0, m, n, ux_mean=0.0, uy_mean=0.0):
+    """(rho, ux, uy) float64 arrays (ny, nx) of the rotated shear wave,
+    optionally carried by a uniform mean flow (ux_mean, uy_mean)."""
     ph = shear_wave_phase(nx, ny, m, n)
     s = np.sin(2.0 * np.pi * ph)
     ex, ey = shear_wave_direction(nx, ny, m, n)
     rho = np.full((ny, nx), float(rho0))
-    return rho, u0 * ex * s, u0 * ey * s
+    return rho, ux_mean + u0 * ex * s, uy_mean + u0 * ey * s
+
+
+def shear_wave_gradients(nx, ny, u0, m, n):
+    """Analytic velocity gradient of the shear wave, shape (2, 2, ny, nx):
+    grad[a, b] = d_b u_a = u0 cos(k . x) e_perp_a k_b (the mean flow drops out)."""
+    ph = shear_wave_phase(nx, ny, m, n)
+    c = np.cos(2.0 * np.pi * ph)
+    e = shear_wave_direction(nx, ny, m, n)
+    k = (2.0 * math.pi * m / nx, 2.0 * math.pi * n / ny)
+    return np.stack([np.stack([u0 * e[a] * k[b] * c for b in range(2)]) for a in range(2)])
 
 
 def shear_wave_window(nx, ny, rho0, u0, m, n, x0, y0, wx, wy):
@@ -115,6 +128,10 @@ class LatticeCase:
     rho_right: float = 0.75
     x_split: int = 0
     steps: int = 0
+    ux_mean: float = 0.0        # uniform mean flow under the shear wave
+    uy_mean: float = 0.0
+    first_order: bool = False   # start from f^eq + f^(1) of Eq. 5 (shear only)
+    boundary: str = "periodic"  # or "walls_x": bounce-back wall columns x = 0, nx - 1
 
     @property
     def nodes(self) -> int:
@@ -122,8 +139,15 @@ class LatticeCase:
 
     def fields(self):
         if self.case == "shear":
-            return shear_wave_fields(self.nx, self.ny, self.rho0, self.u0, self.m, self.n)
+            return shear_wave_fields(self.nx, self.ny, self.rho0, self.u0, self.m, self.n,
+                                     self.ux_mean, self.uy_mean)
         return shock_tube_fields(self.nx, self.ny, self.rho_left, self.rho_right, self.x_split)
+
+    def gradients(self):
+        """grad[a, b] = d_b u_a of the initial velocity field (shear only)."""
+        if self.case != "shear":
+            raise ValueError("analytic gradients exist for the shear wave only")
+        return shear_wave_gradients(self.nx, self.ny, self.u0, self.m, self.n)
 
 
 def shear_64(coll: str = "oreg", m: int = 2, n: int = 1) -> LatticeCase:
@@ -138,6 +162,19 @@ def shock_2048x4(eq: str = "guided", coll: str = "oreg") -> LatticeCase:
                        rho_left=1.5, rho_right=0.75, x_split=1024, steps=2000)
 
 
+def shock_tube_walls(theta: float = 0.35, nu: float = 1e-5, nx: int = 800, ny: int = 1,
+                     eq: str = "guided", coll: str = "oreg", rho_left: float = 1.5,
+                     rho_right: float = 0.75, steps: int = 500) -> LatticeCase:
+    """Isothermal shock tube between full-way bounce-back walls (Sec. IV,
+    Figs. 3-4): nx x ny lattice, wall columns x = 0 and nx - 1, density step
+    at the middle, tau = 1/2 + nu / theta.  The paper runs 800 x 1 for 500
+    steps at (theta, nu) = (0.35, 1e-5) and (0.4, 1e-9) and does not state
+    the two densities; 1.5 | 0.75 is used as for the periodic tube."""
+    return LatticeCase(nx=nx, ny=ny, tau=0.5 + nu / theta, theta=theta, eq=eq, coll=coll,
+                       case="shock", rho_left=rho_left, rho_right=rho_right, x_split=nx // 2,
+                       steps=steps, boundary="walls_x")
+
+
 def large_shear(theta: float = THETA0, seed: int = 0, side: int = 8192,
                 steps: int = 500) -> LatticeCase:
     """side x side rotated shear wave at a seeded random angle, tau = 0.6."""
@@ -146,6 +183,28 @@ def large_shear(theta: float = THETA0, seed: int = 0, side: int = 8192,
     m, n, _ = wave_vector_from_angle(side, side, phi)
     return LatticeCase(nx=side, ny=side, tau=0.6, theta=theta, case="shear",
                        u0=0.05, m=m, n=n, steps=steps)
+
+
+def mach_wave(geometry: str, mach: float, coll: str = "oreg", nu: float = 0.01,
+              theta: float = THETA0, amplitude: float = 1e-3, length: int = 200,
+              steps: int = 20000, first_order: bool = True) -> LatticeCase:
+    """Decaying shear wave on a mean flow u_y = Ma sqrt(theta) (Sec. IV, Fig. 2).
+
+    ``axis``: u_x = A0 sin(2 pi y / L) on a 4 x L lattice, wave vector along y.
+    ``diagonal``: the pi/4 wave, u = (A0, A0) sin(k . x) with k along (-1, 1) on
+    an M x M lattice, M = round(L sqrt 2), so the wavelength is L as in the
+    axis case.  tau = 1/2 + nu / theta."""
+    tau = 0.5 + nu / theta
+    if geometry == "axis":
+        nx, ny, m, n, u0 = 4, length, 0, 1, amplitude
+    elif geometry == "diagonal":
+        side = int(round(length * math.sqrt(2.0)))
+        nx, ny, m, n, u0 = side, side, -1, 1, amplitude * math.sqrt(2.0)
+    else:
+        raise ValueError(f"unknown geometry {geometry!r}")
+    return LatticeCase(nx=nx, ny=ny, tau=tau, theta=theta, coll=coll, case="shear", u0=u0,
+                       m=m, n=n, steps=steps, uy_mean=mach * math.sqrt(theta),
+                       first_order=first_order)
 
 
 def _log_uniform_int(rng, lo, hi):

@@ -23,6 +23,15 @@ invariants.  None is produced by re-running the oracle's own formula:
 * Conservation under periodic boundaries; the viscous decay of a shear wave
   exp(-nu k^2 t), nu = theta (tau - 1/2) (Eq. 14a, Sec. IV); the isothermal
   Riemann problem (Sec. IV shock tube, textbook solution in riemann.py).
+* Eq. 5 (first-order populations from a velocity gradient): their mass,
+  momentum and stress are the paper's Eqs. 12-13 / 16-17; a wave started
+  from them decays at the viscous rate from the first step.
+* Fig. 2a: an axis-aligned shear wave on a mean flow along its wave vector
+  decays at the imposed viscosity and is advected at U.k.
+* Full-way bounce-back walls: exact mass, the rest state as a fixed point,
+  the slowest viscous mode between no-slip walls placed halfway between wall
+  and fluid columns, and the Sec. IV shock tube between walls against the
+  Riemann solution at the paper's temperatures and viscosities.
 """
 from __future__ import annotations
 
@@ -205,6 +214,56 @@ def check_foreg_poly2_closed_forms():
         _close(Pi[1, 1], -sxx - uy * phi[1] + 4.5 * uy ** 2 * sxx, 1e-15, "Eq. 17 yy")
 
 
+def _first_order_cases(eq):
+    rng = np.random.default_rng(RNG_SEED + 11 + eq)
+    for k in range(40):
+        rho = rng.uniform(0.6, 1.8)
+        ux, uy = (0.0, 0.0) if k < 4 else rng.uniform(-0.25, 0.25, 2)
+        theta = (rng.uniform(0.25, 0.45) if k % 2 else 1.0 / 3.0) if eq == O.GUIDED else 1.0 / 3.0
+        tau = rng.uniform(0.51, 2.0)
+        grad = rng.uniform(-0.01, 0.01, (2, 2))
+        yield rho, ux, uy, theta, tau, grad
+
+
+def check_first_order_closed_forms():
+    """Eq. 5 populations against the paper's own moments of them: Eq. 12 is
+    the pressure tensor and Eq. 13 the mass/momentum of f^(1) with the guided
+    equilibrium, Eqs. 16-17 with the polynomial one.  With the strain rate
+    written as the trace-free stress S = -tau rho theta (grad u + grad u^T -
+    div u I): S_xx = -tau rho theta (d_x u_x - d_y u_y),
+    S_xy = -tau rho theta (d_x u_y + d_y u_x)."""
+    c = _c()
+    for eq in (O.GUIDED, O.POLY2):
+        for rho, ux, uy, th, tau, g in _first_order_cases(eq):
+            f1 = O.first_order(tau, eq, th, rho, ux, uy, g)
+            te = th if eq == O.GUIDED else 1.0 / 3.0
+            sxx = -tau * rho * te * (g[0, 0] - g[1, 1])
+            sxy = -tau * rho * te * (g[1, 0] + g[0, 1])
+            _close(f1.sum(), 0.0, 1e-16, "Eq. 13a/16a <f^(1),1> = 0")
+            mom = c.T @ f1
+            Pi = np.einsum("ia,ib,i->ab", c, c, f1)
+            if eq == O.GUIDED:
+                _close(mom[0], -sxx * ux * (3 * th + ux ** 2 - 1) / (2 * th ** 2), 1e-16,
+                       "Eq. 13b x of f^(1)")
+                _close(mom[1], sxx * uy * (3 * th + uy ** 2 - 1) / (2 * th ** 2), 1e-16,
+                       "Eq. 13b y of f^(1)")
+                _close(Pi[0, 0], sxx * (th - ux ** 2) * (1 - th - ux ** 2) / (2 * th ** 2), 1e-16,
+                       "Eq. 12b xx of f^(1)")
+                _close(Pi[1, 1], -sxx * (th - uy ** 2) * (1 - th - uy ** 2) / (2 * th ** 2),
+                       1e-16, "Eq. 12b yy of f^(1)")
+                _close(Pi[0, 1], sxy - sxx * ux * uy * (ux ** 2 - uy ** 2) / (2 * th ** 2), 1e-16,
+                       "Eq. 12a/12c xy of f^(1)")
+            else:
+                br = (ux ** 2 - uy ** 2) * sxx + 2 * ux * uy * sxy
+                phi = np.array([-4.5 * ux * br, -4.5 * uy * br])
+                _close(mom, phi, 1e-16, "Eq. 16b of f^(1)")
+                _close(Pi[0, 1], sxy - uy * phi[0], 1e-16, "Eq. 17 xy of f^(1)")
+                _close(Pi[0, 0], sxx - ux * phi[0] - 4.5 * ux ** 2 * sxx, 1e-16,
+                       "Eq. 17 xx of f^(1)")
+                _close(Pi[1, 1], -sxx - uy * phi[1] + 4.5 * uy ** 2 * sxx, 1e-16,
+                       "Eq. 17 yy of f^(1)")
+
+
 def check_foreg_vanishes_without_stress():
     rng = np.random.default_rng(RNG_SEED + 7)
     for eq in (O.GUIDED, O.POLY2):
@@ -363,6 +422,68 @@ def check_shear_wave_decay_off_reference_temperature():
         assert abs(r / want[coll] - 1) < 1e-2, f"coll={coll}: {r} vs linear theory {want[coll]}"
 
 
+def _wave_series(case, steps, every):
+    """Oracle run of a shear-wave case; samples t, and both quadratures of the
+    mode projection (2/N) sum u.e_perp {sin, cos}(k.x)."""
+    p = O.params(case.nx, case.ny, case.tau, case.theta,
+                 O.GUIDED if case.eq == "guided" else O.POLY2,
+                 O.OREG if case.coll == "oreg" else O.BGK)
+    rho, ux, uy = case.fields()
+    if case.first_order:
+        f = O.init_first_order(p, rho, ux, uy, case.gradients())
+    else:
+        f = O.init_equilibrium(p, rho, ux, uy)
+    ph = 2 * np.pi * W.shear_wave_phase(case.nx, case.ny, case.m, case.n)
+    sn, cs = np.sin(ph), np.cos(ph)
+    ex, ey = W.shear_wave_direction(case.nx, case.ny, case.m, case.n)
+    ts, a_s, a_c = [], [], []
+    for t in range(0, steps + 1, every):
+        _, vx, vy, _ = O.fields(f)
+        up = vx * ex + vy * ey
+        ts.append(t)
+        a_s.append(2.0 / case.nodes * np.sum(up * sn))
+        a_c.append(2.0 / case.nodes * np.sum(up * cs))
+        if t < steps:
+            f = O.run(f, p, every)
+    return np.array(ts, float), np.array(a_s), np.array(a_c)
+
+
+def check_first_order_start():
+    """Starting from f^eq + f^(1) (Eq. 5) puts the wave on its viscous decay
+    exp(-nu k^2 t) (Eq. 14a) from the first step; an equilibrium start (no
+    stress) first jumps by O(1e-3) of the amplitude before it settles."""
+    k2 = W.wave_number_sq(64, 64, 2, 1)
+    for coll in ("oreg", "bgk"):
+        for tau in (0.53, 0.8):
+            nu = (tau - 0.5) / 3.0
+            dev = {}
+            for first_order in (False, True):
+                case = W.LatticeCase(nx=64, ny=64, tau=tau, coll=coll, m=2, n=1, u0=0.05,
+                                     first_order=first_order)
+                ts, a_s, _ = _wave_series(case, 20, 1)
+                dev[first_order] = np.max(np.abs(a_s / (a_s[0] * np.exp(-nu * k2 * ts)) - 1))
+            assert dev[True] < 2e-4, (coll, tau, dev)
+            assert dev[False] > 2e-3, (coll, tau, dev)
+
+
+def check_mean_flow_axis_wave():
+    """Sec. IV, Fig. 2a: a shear wave whose wave vector is along a lattice axis,
+    carried along that axis by a mean flow u_y = Ma sqrt(theta), decays at the
+    imposed viscosity for OReg and BGK alike, and is advected rigidly: its
+    phase turns at U.k (Galilean invariance of the Navier-Stokes limit)."""
+    for ma in (0.0, 0.2, 0.4):
+        for coll in ("oreg", "bgk"):
+            case = W.mach_wave("axis", ma, coll, length=64, steps=2000)
+            ts, a_s, a_c = _wave_series(case, case.steps, 10)
+            gamma = -np.polyfit(ts, np.log(np.hypot(a_s, a_c)), 1)[0]
+            ratio = gamma / W.wave_number_sq(case.nx, case.ny, case.m, case.n) / (
+                case.theta * (case.tau - 0.5))
+            assert abs(ratio - 1) < 2e-3, (ma, coll, ratio)
+            omega = -np.polyfit(ts, np.unwrap(np.arctan2(a_c, a_s)), 1)[0]
+            want = case.uy_mean * 2 * np.pi * case.n / case.ny
+            assert abs(omega - want) <= 1e-4 * abs(want) + 1e-12, (ma, coll, omega, want)
+
+
 def check_shock_tube():
     """Sec. IV shock tube at theta = 1/3 vs the exact isothermal Riemann
     solution; OReg shows no post-shock oscillation, BGK does."""
@@ -387,12 +508,95 @@ def check_shock_tube():
     assert tv[O.BGK] > 3 * tv[O.OREG], tv
 
 
+# ---------------------------------------------------------------------------
+# full-way bounce-back wall columns (Sec. IV shock tube)
+# ---------------------------------------------------------------------------
+
+def check_walls_conservation():
+    """Bounce-back only permutes populations: the mass summed over all nodes
+    (walls included) stays exact, and a uniform fluid at rest, whose
+    populations are symmetric under c -> -c, is a fixed point."""
+    rng = np.random.default_rng(RNG_SEED + 21)
+    nx, ny = 19, 5
+    for coll in (O.OREG, O.BGK):
+        p = O.params(nx, ny, 0.7, 1 / 3, O.GUIDED, coll, walls=True)
+        f = O.init_equilibrium(p, rng.uniform(0.8, 1.2, (ny, nx)),
+                               rng.uniform(-0.05, 0.05, (ny, nx)),
+                               rng.uniform(-0.05, 0.05, (ny, nx)))
+        g = O.run(f, p, 300)
+        _close(g.sum() / f.sum() - 1, 0.0, 1e-13, "mass with walls")
+        rest = O.init_equilibrium(p, np.full((ny, nx), 1.1), np.zeros((ny, nx)),
+                                  np.zeros((ny, nx)))
+        assert np.array_equal(O.run(rest, p, 7), rest), "rest state with walls moved"
+    post = np.zeros(9)
+    f = rng.uniform(0.1, 0.5, 9)
+    O.lib().ora_bounce_back_node(O._p(f), O._p(post))
+    c = _c()
+    for i in range(9):
+        k = [j for j in range(9) if (c[j] == -c[i]).all()][0]
+        assert post[i] == f[k], "bounce-back must return f_opp(i) along c_i"
+
+
+def check_walls_shear_decay():
+    """No-slip walls halfway between the wall columns and the first fluid
+    columns: u_y = A sin(pi (x - 1/2) / L), L = nx - 2, is the slowest
+    Navier-Stokes mode between walls at x = 1/2 and x = nx - 3/2 and decays
+    as exp(-nu (pi / L)^2 t), nu = theta (tau - 1/2)."""
+    nx, ny = 66, 2
+    L = nx - 2
+    x = np.arange(nx)
+    prof = np.sin(np.pi * (x - 0.5) / L)
+    prof[0] = prof[-1] = 0.0
+    for coll in (O.OREG, O.BGK):
+        for tau in (0.6, 0.8):
+            p = O.params(nx, ny, tau, 1 / 3, O.GUIDED, coll, walls=True)
+            f = O.init_equilibrium(p, np.ones((ny, nx)), np.zeros((ny, nx)),
+                                   1e-3 * prof[None, :] * np.ones((ny, 1)))
+            ts, amps = [], []
+            for t in range(0, 4001, 100):
+                vy = O.fields(f)[2]
+                if t >= 200:
+                    ts.append(t)
+                    amps.append(np.sum(vy[0, 1:-1] * prof[1:-1]))
+                f = O.run(f, p, 100)
+            gamma = -np.polyfit(ts, np.log(amps), 1)[0]
+            ratio = gamma / ((tau - 0.5) / 3 * (np.pi / L) ** 2)
+            assert abs(ratio - 1) < 1e-3, (coll, tau, ratio)
+
+
+def check_walls_shock_tube():
+    """Sec. IV, Figs. 3-4: the shock tube between bounce-back walls on 800 x 1
+    cells, 500 steps, at (theta, nu) = (0.35, 1e-5) and (0.4, 1e-9).  OReg
+    matches the exact isothermal Riemann solution (c_s = sqrt(theta)) to the
+    paper's ~98-99% L2 accuracy with no spurious oscillation (total
+    variation within 1% of the exact profile's); BGK oscillates."""
+    for theta, nu, acc in ((0.35, 1e-5, 0.985), (0.4, 1e-9, 0.98)):
+        case = W.shock_tube_walls(theta=theta, nu=nu)
+        x = np.arange(case.nx)
+        rho_ex, _ = riemann.solution((x - (case.x_split - 0.5)) / case.steps,
+                                     case.rho_left, case.rho_right, theta)
+        fluid = (x >= 1) & (x <= case.nx - 2)
+        tv_exact = np.abs(np.diff(rho_ex[fluid])).sum()
+        tv = {}
+        for coll in (O.OREG, O.BGK):
+            p = O.params(case.nx, case.ny, case.tau, theta, O.GUIDED, coll, walls=True)
+            rho = O.fields(O.run(O.init_equilibrium(p, *case.fields()), p, case.steps))[0][0]
+            tv[coll] = np.abs(np.diff(rho[fluid])).sum() / tv_exact
+            if coll == O.OREG:
+                l2 = np.sqrt(((rho[fluid] - rho_ex[fluid]) ** 2).sum() / (rho_ex[fluid] ** 2).sum())
+                assert 1 - l2 >= acc, (theta, nu, l2)
+                assert abs(tv[coll] - 1) < 0.01, (theta, nu, tv)
+        assert tv[O.BGK] > 10, (theta, nu, tv)
+
+
 FAST_CHECKS = [
     check_velocity_set, check_guided_rest_weights, check_poly2_rest_weights,
     check_equilibrium_moments, check_foreg_mass_zero, check_foreg_guided_closed_forms,
-    check_foreg_poly2_closed_forms, check_foreg_vanishes_without_stress,
+    check_foreg_poly2_closed_forms, check_first_order_closed_forms,
+    check_foreg_vanishes_without_stress,
     check_collision_special_cases, check_streaming_translation,
     check_uniform_state_is_fixed, check_conservation,
 ]
 LATTICE_CHECKS = [check_shear_wave_decay, check_shear_wave_decay_off_reference_temperature,
-                  check_shock_tube]
+                  check_first_order_start, check_mean_flow_axis_wave, check_shock_tube,
+                  check_walls_conservation, check_walls_shear_decay, check_walls_shock_tube]

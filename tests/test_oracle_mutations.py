@@ -50,6 +50,25 @@ MUTATIONS = [
      "const int64_t yd = ora_wrap(y - ORA_C[i][1], ny);\n                const int64_t xd = ora_wrap(x + ORA_C[i][0], nx);\n                dst"),
     ("stream transposed", "dst[i * N + yd * nx + xd] = post[i];",
      "dst[i * N + (xd * ny + yd)] = post[i];"),
+    ("first-order sign", "f1[i] = -tau * feq[i] * contraction", "f1[i] = tau * feq[i] * contraction"),
+    ("first-order tau - 1/2 for tau", "f1[i] = -tau * feq[i] * contraction",
+     "f1[i] = -(tau - 0.5) * feq[i] * contraction"),
+    ("first-order absolute velocity", "Cp[a] = (double)ORA_C[i][a] - u[a]",
+     "Cp[a] = (double)ORA_C[i][a]"),
+    ("first-order theta squared", "grad[b * ORA_D + a]) / (2.0 * theta_eff)",
+     "grad[b * ORA_D + a]) / (2.0 * theta_eff * theta_eff)"),
+    ("first-order delta term dropped", "(Cp[a] * Cp[b] - Cp2 * delta / (double)ORA_D)",
+     "(Cp[a] * Cp[b])"),
+    ("first-order start without f1", "f[i * N + n] = feq[i] + f1[i];", "f[i * N + n] = feq[i];"),
+    ("first-order gradient components swapped", "g[ab] = grad[ab * N + n]",
+     "g[ab] = grad[(3 - ab) * N + n]"),
+    ("bounce-back keeps the direction", "ORA_C[k][1] == -ORA_C[i][1]) post[i] = f[k];",
+     "ORA_C[k][1] == -ORA_C[i][1]) post[i] = f[i];"),
+    ("specular instead of bounce-back", "ORA_C[k][1] == -ORA_C[i][1]) post[i]",
+     "ORA_C[k][1] == ORA_C[i][1]) post[i]"),
+    ("wall column off by one", "if (p->walls && (x == 0 || x == nx - 1))",
+     "if (p->walls && (x == 1 || x == nx - 1))"),
+    ("walls ignored", "if (p->walls && (x == 0 || x == nx - 1))", "if (0)"),
     ("streaming-only path wraps the wrong axis", "ora_wrap(x + ORA_C[i][0], nx);\n                dst[i * N + yd * nx + xd] = post[i * N",
      "ora_wrap(x + ORA_C[i][1], nx);\n                dst[i * N + yd * nx + xd] = post[i * N"),
 ]
