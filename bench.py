@@ -347,6 +347,7 @@ def run_native(args):
         extra["precision_vs_fp64"] = precision_section(args)
         extra["batched"] = batched_section(args)
         extra["serving"] = serving_section(args, extra["batched"])
+        extra["mach_sweep"] = mach_sweep_section()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -494,6 +495,28 @@ def precision_section(args):
     den = np.abs(f["f64"]).max()
     return {"workload": f"{side}x{side} shear wave, tau={c.tau}, {steps} steps",
             **{st: float(f"{np.abs(f[st] - f['f64']).max() / den:.3e}") for st in ("f32", "f16", "bf16")}}
+
+
+def mach_sweep_section():
+    """nu~/nu of the decaying shear wave on a mean flow u_y = Ma sqrt(theta)
+    (Sec. IV, Fig. 2): wavelength 200, nu = 0.01 (tau = 0.53), amplitude 1e-3,
+    FP64 storage, first-order start (Eq. 5), 20000 steps per lattice."""
+    from paper_2501_16000_gb300 import analysis
+    t0 = time.perf_counter()
+    rows = analysis.mach_sweep(machs=(0.0, 0.1, 0.2, 0.3, 0.4), length=200, steps=20000,
+                               every=200)
+    out = {"workload": "axis: 4x200, k along y; diagonal: 283x283, k along (-1, 1); "
+                       "mean flow (0, Ma sqrt(1/3)); nu = 0.01; f64; 20000 steps",
+           "wall_s": round(time.perf_counter() - t0, 2)}
+    for r in rows:
+        g, ma = r["geometry"], f"{r['mach']:.1f}"
+        unstable = r.get("unstable", False)
+        out.setdefault(g + "_nu_ratio", {}).setdefault(ma, {})[r["coll"]] = (
+            "unstable" if unstable else round(r["nu_ratio"], 5))
+        if r["mach"] > 0 and not unstable:
+            out.setdefault(g + "_phase_rate_over_Uk", {}).setdefault(ma, {})[r["coll"]] = round(
+                r["omega"] / r["omega_advect"], 5)
+    return out
 
 
 def lat_bytes(storage, N):

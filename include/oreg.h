@@ -71,8 +71,17 @@ typedef enum {
  * and write to the neighbours.  Same results, half the memory. */
 typedef enum { OLB_LAYOUT_AB = 0, OLB_LAYOUT_AA = 1 } olb_layout;
 
+/* PERIODIC: periodic in x and y.  WALLS_X: columns x = 0 and x = nx - 1 are
+ * solid wall nodes with full-way bounce-back (the shock tube of Sec. IV):
+ * a wall node does not collide, it returns every population along the link
+ * it arrived on, post_i = f_opp(i), so the no-slip wall lies halfway between
+ * the wall column and the first fluid column; y stays periodic.  Wall nodes
+ * keep populations in the state (moments there are not fluid fields); the
+ * total mass over all nodes stays exactly conserved.  Needs nx >= 3. */
+typedef enum { OLB_BOUNDARY_PERIODIC = 0, OLB_BOUNDARY_WALLS_X = 1 } olb_boundary;
+
 typedef struct {
-    int32_t nx, ny;        /* lattice size, >= 1 each; periodic in x and y */
+    int32_t nx, ny;        /* lattice size, >= 1 each */
     double tau;            /* relaxation time, > 0.5 */
     double theta;          /* guided: lattice temperature in (0, 1);
                               poly2: must be 1/3 (theta0 of Eq. 15) */
@@ -88,6 +97,7 @@ typedef struct {
     size_t buffer_bytes;   /* size of device_buffer in bytes (ignored if NULL) */
     void *cuda_stream;     /* cudaStream_t for all work of this lattice;
                               NULL: the library creates and owns one */
+    int32_t boundary;      /* olb_boundary (0: periodic) */
 } olb_params;
 
 /* Tuning and precision options of a lattice (olb_set_option). */
@@ -113,7 +123,8 @@ typedef enum {
     OLB_OPT_STOCHASTIC_ROUNDING = 3
 } olb_option;
 
-/* Version of this ABI (bumped on incompatible change). */
+/* Version of this ABI (bumped on incompatible change); 2 since
+ * olb_params.boundary. */
 int32_t olb_abi_version(void);
 
 /* Bytes of device memory the populations of a lattice with these
@@ -132,6 +143,19 @@ olb_status olb_create_lattice(const olb_params *p, olb_lattice **out);
  * e_perp = (-k_y, k_x)/|k|, rho = rho0.  (m, n) != (0, 0).  Sets t = 0. */
 olb_status olb_init_shear_wave(olb_lattice *lat, double rho0, double u0, int32_t m,
                                int32_t n);
+
+/* The same shear wave carried by a uniform mean flow U = (ux_mean, uy_mean):
+ * u = U + u0 sin(k.x) e_perp (the Mach sweep of Sec. IV, Fig. 2, uses
+ * U = (0, Ma sqrt(theta))).  first_order = 0 starts from S_0 = f^eq;
+ * first_order = 1 starts from S_0 = f^eq + f^(1), the first-order
+ * populations of Eq. 5 evaluated with the analytic velocity gradient
+ * grad_b u_a = u0 cos(k.x) e_perp,a k_b, the lattice's tau and the theta of
+ * Eq. 6 (the lattice theta for the guided equilibrium, 1/3 for the
+ * polynomial one); this removes the start-up transient of an equilibrium
+ * start.  OLB_ERR_INVALID for (m, n) = (0, 0), rho0 <= 0, non-finite
+ * u0 / U, or first_order not 0 or 1.  Sets t = 0. */
+olb_status olb_init_shear_flow(olb_lattice *lat, double rho0, double u0, int32_t m, int32_t n,
+                               double ux_mean, double uy_mean, int32_t first_order);
 
 /* S_0 = f^eq of the isothermal shock tube (Sec. IV): rho = rho_left for
  * x < x_split, rho_right otherwise, u = 0.  Sets t = 0. */
@@ -190,6 +214,16 @@ olb_status olb_diagnostics(olb_lattice *lat, double *mass, double *mom_x, double
  * A = (2 / (nx ny)) sum_x u(x) . e_perp sin(k . x), k = 2 pi (m/nx, n/ny);
  * the decay statistic of Sec. IV.  Synchronises the stream. */
 olb_status olb_wave_amplitude(olb_lattice *lat, int32_t m, int32_t n, double *amp);
+
+/* Both quadratures of that projection,
+ * a_sin = (2 / (nx ny)) sum_x u(x) . e_perp sin(k . x) (= olb_wave_amplitude) and
+ * a_cos = (2 / (nx ny)) sum_x u(x) . e_perp cos(k . x),
+ * so that a wave advected by a mean flow has amplitude hypot(a_sin, a_cos)
+ * and phase atan2(a_cos, a_sin).  Either pointer may be NULL, not both.
+ * Returns OLB_ERR_NONFINITE if the state holds non-finite populations.
+ * Synchronises the stream. */
+olb_status olb_wave_mode(olb_lattice *lat, int32_t m, int32_t n, double *a_sin,
+                         double *a_cos);
 
 /* ------------------------------------------------------------------------
  * Batched path: many independent lattices advanced together.

@@ -55,7 +55,8 @@ class BatchEngine:
         """A lattice of a ``workloads.LatticeCase`` on this batch's stream,
         initialised (not yet added)."""
         lat = Lattice(case.nx, case.ny, case.tau, case.theta, case.eq, case.coll, self.storage,
-                      self.layout, torch_memory=True, stream=self.stream, **kw)
+                      self.layout, torch_memory=True, stream=self.stream,
+                      boundary=case.boundary, **kw)
         lat.init_case(case)
         return lat
 

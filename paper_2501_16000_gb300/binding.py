@@ -43,7 +43,11 @@ class olb_params(ctypes.Structure):
                 ("eq", ctypes.c_int32), ("coll", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("device_buffer", ctypes.c_void_p), ("buffer_bytes", ctypes.c_size_t),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("boundary", ctypes.c_int32)]
+
+
+ABI_VERSION = 2
+BOUNDARY = {"periodic": 0, "walls_x": 1}
 
 
 class olb_batch_params(ctypes.Structure):
@@ -65,6 +69,9 @@ SIGNATURES = {
     "olb_set_option": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int64]),
     "olb_init_shear_wave": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int32, ctypes.c_int32]),
+    "olb_init_shear_flow": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int32]),
     "olb_init_shock_tube": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int32]),
     "olb_init_fields": (ctypes.c_int, [_h, _d, _d, _d]),
@@ -79,6 +86,7 @@ SIGNATURES = {
     "olb_set_populations": (ctypes.c_int, [_h, _d, ctypes.c_int64]),
     "olb_diagnostics": (ctypes.c_int, [_h, _d, _d, _d, _P(ctypes.c_int64)]),
     "olb_wave_amplitude": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32, _d]),
+    "olb_wave_mode": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32, _d, _d]),
     "olb_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, _P(olb_params), ctypes.c_int64,
                                                ctypes.c_void_p]),
     "olb_destroy": (ctypes.c_int, [_h]),
@@ -117,6 +125,10 @@ def load() -> ctypes.CDLL:
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
+            if lib.olb_abi_version() != ABI_VERSION:
+                raise OregLibraryMissing(
+                    f"{path} implements ABI {lib.olb_abi_version()}, this binding {ABI_VERSION}: "
+                    "rebuild it with `python -m paper_2501_16000_gb300.build`")
             _lib = lib
         return _lib
 

@@ -87,6 +87,10 @@ olb_status validate(const olb_params *p) {
         return fail(OLB_ERR_INVALID, "guided equilibrium needs 0 < theta < 1 (got %g)", p->theta);
     if (p->eq == OLB_EQ_POLY2 && std::fabs(p->theta - 1.0 / 3.0) > 1e-12)
         return fail(OLB_ERR_INVALID, "polynomial equilibrium is defined at theta = 1/3 only (got %.17g)", p->theta);
+    if (p->boundary != OLB_BOUNDARY_PERIODIC && p->boundary != OLB_BOUNDARY_WALLS_X)
+        return fail(OLB_ERR_INVALID, "unknown boundary %d", p->boundary);
+    if (p->boundary == OLB_BOUNDARY_WALLS_X && p->nx < 3)
+        return fail(OLB_ERR_INVALID, "wall columns need nx >= 3 (got %d)", p->nx);
     return OLB_OK;
 }
 
@@ -280,7 +284,7 @@ olb_status mode_tables(olb_lattice *L, int m, int n) {
 
 extern "C" {
 
-int32_t olb_abi_version(void) { return 1; }
+int32_t olb_abi_version(void) { return 2; }
 
 size_t olb_required_bytes(const olb_params *p) {
     if (validate(p) != OLB_OK) return 0;
@@ -384,12 +388,17 @@ olb_status olb_set_option(olb_lattice *L, int32_t option, int64_t value) {
     }
 }
 
-olb_status olb_init_shear_wave(olb_lattice *L, double rho0, double u0, int32_t m, int32_t n) {
+olb_status olb_init_shear_flow(olb_lattice *L, double rho0, double u0, int32_t m, int32_t n,
+                               double ux_mean, double uy_mean, int32_t first_order) {
     olb_status st = check_lattice(L, false);
     if (st != OLB_OK) return st;
     if (m == 0 && n == 0) return fail(OLB_ERR_INVALID, "wave vector (m, n) must not be (0, 0)");
     if (!(std::isfinite(rho0) && rho0 > 0 && std::isfinite(u0)))
         return fail(OLB_ERR_INVALID, "rho0 must be > 0 and u0 finite");
+    if (!(std::isfinite(ux_mean) && std::isfinite(uy_mean)))
+        return fail(OLB_ERR_INVALID, "mean flow must be finite");
+    if (first_order != 0 && first_order != 1)
+        return fail(OLB_ERR_INVALID, "first_order must be 0 or 1 (got %d)", first_order);
     InitSpec s{};
     s.mode = INIT_SHEAR;
     s.rho_a = rho0;
@@ -400,7 +409,18 @@ olb_status olb_init_shear_wave(olb_lattice *L, double rho0, double u0, int32_t m
     const double nk = std::hypot(kx, ky);
     s.ex = -ky / nk;
     s.ey = kx / nk;
+    s.ux_mean = ux_mean;
+    s.uy_mean = uy_mean;
+    s.first_order = first_order;
+    const double two_pi = 6.283185307179586476925286766559;
+    s.kx = two_pi * kx;
+    s.ky = two_pi * ky;
+    s.tau = L->p.tau;
     return run_init(L, s);
+}
+
+olb_status olb_init_shear_wave(olb_lattice *L, double rho0, double u0, int32_t m, int32_t n) {
+    return olb_init_shear_flow(L, rho0, u0, m, n, 0.0, 0.0, 0);
 }
 
 olb_status olb_init_shock_tube(olb_lattice *L, double rho_left, double rho_right, int32_t x_split) {
@@ -465,6 +485,7 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     a.layout = L->p.layout;
     a.comp = L->comp;
     a.sr = L->sr;
+    a.walls = L->p.boundary == OLB_BOUNDARY_WALLS_X;
     a.warps_per_block = L->warps_per_block;
     a.kconst = L->p.storage == OLB_F64 ? static_cast<const void *>(&L->kd)
                                        : static_cast<const void *>(&L->kf);
@@ -630,10 +651,10 @@ olb_status olb_diagnostics(olb_lattice *L, double *mass, double *mom_x, double *
     return OLB_OK;
 }
 
-olb_status olb_wave_amplitude(olb_lattice *L, int32_t m, int32_t n, double *amp) {
+olb_status olb_wave_mode(olb_lattice *L, int32_t m, int32_t n, double *a_sin, double *a_cos) {
     olb_status st = check_lattice(L, true);
     if (st != OLB_OK) return st;
-    if (!amp) return fail(OLB_ERR_INVALID, "amp must not be NULL");
+    if (!a_sin && !a_cos) return fail(OLB_ERR_INVALID, "a_sin and a_cos must not both be NULL");
     if (m == 0 && n == 0) return fail(OLB_ERR_INVALID, "wave vector (m, n) must not be (0, 0)");
     ModeSpec mode{};
     mode.active = 1;
@@ -649,9 +670,16 @@ olb_status olb_wave_amplitude(olb_lattice *L, int32_t m, int32_t n, double *amp)
     double r[RED_QUANTITIES];
     st = reduce(L, mode, r);
     if (st != OLB_OK) return st;
-    *amp = 2.0 * r[4] / ((double)L->p.nx * L->p.ny);
+    const double scale = 2.0 / ((double)L->p.nx * L->p.ny);
+    if (a_sin) *a_sin = scale * r[4];
+    if (a_cos) *a_cos = scale * r[5];
     if (r[3] > 0) return fail(OLB_ERR_NONFINITE, "state holds non-finite populations");
     return OLB_OK;
+}
+
+olb_status olb_wave_amplitude(olb_lattice *L, int32_t m, int32_t n, double *amp) {
+    if (!amp) return fail(OLB_ERR_INVALID, "amp must not be NULL");
+    return olb_wave_mode(L, m, n, amp, nullptr);
 }
 
 olb_status olb_destroy(olb_lattice *L) {

@@ -74,7 +74,7 @@ __global__ void k_init(typename Storage<S>::T *base, StateGeom g, InitSpec spec,
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (long long)g.nx * spec.rows) return;
     const int y = spec.y0 + (int)(n / g.nx), x = (int)(n % g.nx);
-    double rho, ux, uy;
+    double rho, ux, uy, exx = 0.0, eyy = 0.0, exy = 0.0;
     if (spec.mode == INIT_SHEAR) {
         // phase k.x / 2pi reduced exactly: (m x ny + n y nx) mod (nx ny)
         const long long N = (long long)g.nx * g.ny;
@@ -82,8 +82,16 @@ __global__ void k_init(typename Storage<S>::T *base, StateGeom g, InitSpec spec,
         if (num < 0) num += N;
         const double s = sinpi(2.0 * (double)num / (double)N);
         rho = spec.rho_a;
-        ux = spec.u0 * spec.ex * s;
-        uy = spec.u0 * spec.ey * s;
+        ux = spec.ux_mean + spec.u0 * spec.ex * s;
+        uy = spec.uy_mean + spec.u0 * spec.ey * s;
+        if (spec.first_order) {
+            // symmetric strain rate E = (grad u + grad u^T) / 2 of
+            // u0 sin(k.x) e_perp: grad_b u_a = u0 cos(k.x) e_a k_b
+            const double cph = spec.u0 * cospi(2.0 * (double)num / (double)N);
+            exx = cph * spec.ex * spec.kx;
+            eyy = cph * spec.ey * spec.ky;
+            exy = 0.5 * cph * (spec.ex * spec.ky + spec.ey * spec.kx);
+        }
     } else if (spec.mode == INIT_SHOCK) {
         rho = x < spec.x_split ? spec.rho_a : spec.rho_b;
         ux = 0.0;
@@ -95,6 +103,18 @@ __global__ void k_init(typename Storage<S>::T *base, StateGeom g, InitSpec spec,
     }
     double geq[9];
     eq_dev_f64<EQ>(rho, ux, uy, kd, geq);
+    if (spec.mode == INIT_SHEAR && spec.first_order) {
+        // Eq. 5: f_i^(1) = -(tau / theta) f_i^eq (C_ia C_ib - C_i^2 delta_ab / 2) E_ab,
+        // C_i = c_i - u; the contraction with the symmetric E is
+        // (Cx^2 - Cy^2)(Exx - Eyy)/2 + 2 Cx Cy Exy.
+        const double a = -spec.tau / kd.theta;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double Cx = cx_of(i) - ux, Cy = cy_of(i) - uy;
+            const double h = 0.5 * (Cx * Cx - Cy * Cy) * (exx - eyy) + 2.0 * Cx * Cy * exy;
+            geq[i] += a * (geq[i] + kd.shift[dcls(i)]) * h;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i)
         base[canon_index<S>(i, x, y, g)] = Storage<S>::enc((typename Storage<S>::C)geq[i]);
@@ -159,17 +179,19 @@ __global__ void k_moments(const typename Storage<S>::T *base, StateGeom g, int y
 // ---------------------------------------------------------------------------
 // Diagnostics reductions (warp shuffles + shared memory), fixed grid, fixed
 // order: deterministic.  Quantities: 0 sum of g over finite nodes, 1 momentum
-// x, 2 momentum y, 3 non-finite node count, 4 mode projection
-// sum u.e_perp sin(k.x).  The host adds the constant shifts back to the mass
+// x, 2 momentum y, 3 non-finite node count, 4 and 5 mode projections
+// sum u.e_perp sin(k.x) and sum u.e_perp cos(k.x).  The host adds the constant shifts back to the mass
 // (N_finite sum_i s_i).
 //
 // Each thread accumulates in the storage's compute type C with error-free
 // additions (hi + lo pairs, TwoSum), so FP32 formats keep FP64-grade sums
 // while spending FP32 instructions; the per-thread pairs are combined in
-// FP64.  sin(k.x) = sin(a) cos(b) + cos(a) sin(b), a = 2 pi m x / nx,
+// FP64.  sin(k.x) = sin(a) cos(b) + cos(a) sin(b),
+// cos(k.x) = cos(a) cos(b) - sin(a) sin(b), a = 2 pi m x / nx,
 // b = 2 pi n y / ny, from FP64 row/column tables built on the host.
 // ---------------------------------------------------------------------------
-constexpr int RED_Q = 5;
+constexpr int RED_Q = 6;
+static_assert(RED_Q == RED_QUANTITIES, "reduction layout shared with the host");
 constexpr int RED_THREADS = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -193,7 +215,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Storage<S
                                                         ModeSpec mode, double *partials) {
     using ST = Storage<S>;
     using C = typename ST::C;
-    C hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    C hi[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
     double nonfinite = 0.0;
     C sum_shift = 0;
 #pragma unroll
@@ -228,14 +250,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Storage<S
                 jy += C(cy_of(i)) * v[i];
             }
             const C rho = m + sum_shift;
-            const C sn = (C)mode.tab[x] * (C)mode.tab[2 * g.nx + g.ny + y] +
-                         (C)mode.tab[g.nx + x] * (C)mode.tab[2 * g.nx + y];
-            pair_add(hi[3], lo[3], (jx * (C)mode.ex + jy * (C)mode.ey) / rho * sn);
+            const C sa = (C)mode.tab[x], ca = (C)mode.tab[g.nx + x];
+            const C sb = (C)mode.tab[2 * g.nx + y], cb = (C)mode.tab[2 * g.nx + g.ny + y];
+            const C up = (jx * (C)mode.ex + jy * (C)mode.ey) / rho;
+            pair_add(hi[3], lo[3], up * (sa * cb + ca * sb));
+            pair_add(hi[4], lo[4], up * (ca * cb - sa * sb));
         }
     }
     double acc[RED_Q] = {(double)hi[0] + (double)lo[0], (double)hi[1] + (double)lo[1],
                          (double)hi[2] + (double)lo[2], nonfinite,
-                         (double)hi[3] + (double)lo[3]};
+                         (double)hi[3] + (double)lo[3], (double)hi[4] + (double)lo[4]};
     __shared__ double sh[RED_THREADS / 32][RED_Q];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -257,7 +281,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Storage<S
 template <int S>
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double *partials, int nblocks,
                                                               double *out) {
-    double acc[RED_Q] = {0, 0, 0, 0, 0};
+    double acc[RED_Q] = {};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
 #pragma unroll
         for (int q = 0; q < RED_Q; ++q) acc[q] += partials[(size_t)b * RED_Q + q];

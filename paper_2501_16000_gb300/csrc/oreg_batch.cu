@@ -47,6 +47,9 @@ olb_status bcuda(cudaError_t e, const char *what) {
      : (storage) == OLB_F16_SHIFTED ? fn##_f16(__VA_ARGS__)             \
                                     : fn##_bf16(__VA_ARGS__))
 
+// item groups: (walls, equilibrium, collision, parity class)
+constexpr int NGROUPS = 16;
+
 struct Member {
     olb_lattice *lat;
     long long g_base, g_end;  // active global steps [g_base, g_end)
@@ -87,15 +90,16 @@ struct olb_batch {
     // device tables
     char *d_descs;
     int4 *d_items;
-    int *d_groups;          // item offsets of the 8 (eq, coll, parity class) groups
+    int *d_groups;          // item offsets of the 16 (walls, eq, coll, parity class) groups
     long long *d_g;
     // host mirrors
     std::vector<Member> members;
     std::vector<char> h_descs;
     std::vector<int4> h_items;
-    int *h_groups;          // pinned, 9 entries
+    int *h_groups;          // pinned, NGROUPS + 1 entries
     long long G;            // global step counter at the start of the next round
     bool captured;
+    bool graph_walls;       // the captured graph launches the wall-column kernels
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
@@ -105,14 +109,15 @@ namespace {
 olb_status upload(olb_batch *b) {
     const size_t nm = b->members.size();
     b->h_descs.assign(nm * b->desc_size, 0);
-    std::vector<int4> per_group[8];
+    std::vector<int4> per_group[NGROUPS];
     for (size_t j = 0; j < nm; ++j) {
         const Member &m = b->members[j];
         const olb_lattice *L = m.lat;
         if (L->p.storage == OLB_F64) fill_desc<double>(&b->h_descs[j * b->desc_size], m, L->kd);
         else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf);
         const int cls = (int)((m.t_base - m.g_base) & 1);
-        const int grp = (L->p.eq * 2 + L->p.coll) * 2 + cls;
+        const int walls = L->p.boundary == OLB_BOUNDARY_WALLS_X;
+        const int grp = ((walls * 2 + L->p.eq) * 2 + L->p.coll) * 2 + cls;
         const int lw = segment_log2(L->p.nx, L->V);
         const int segs = (L->p.nx + (L->V << lw) - 1) / (L->V << lw);
         const int rows = 32 >> lw;  // rows per warp item
@@ -120,11 +125,11 @@ olb_status upload(olb_batch *b) {
             for (int s = 0; s < segs; ++s) per_group[grp].push_back(make_int4((int)j, y, s, 0));
     }
     b->h_items.clear();
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < NGROUPS; ++q) {
         b->h_groups[q] = (int)b->h_items.size();
         b->h_items.insert(b->h_items.end(), per_group[q].begin(), per_group[q].end());
     }
-    b->h_groups[8] = (int)b->h_items.size();
+    b->h_groups[NGROUPS] = (int)b->h_items.size();
     if ((long long)b->h_items.size() > b->p.max_items)
         return bfail(OLB_ERR_NOMEM, "batch work items %zu exceed max_items %lld", b->h_items.size(),
                      (long long)b->p.max_items);
@@ -136,7 +141,7 @@ olb_status upload(olb_batch *b) {
         B_CUDA(cudaMemcpyAsync(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(int4),
                                cudaMemcpyHostToDevice, b->stream),
                "uploading batch items");
-    B_CUDA(cudaMemcpyAsync(b->d_groups, b->h_groups, 9 * sizeof(int), cudaMemcpyHostToDevice,
+    B_CUDA(cudaMemcpyAsync(b->d_groups, b->h_groups, (NGROUPS + 1) * sizeof(int), cudaMemcpyHostToDevice,
                            b->stream),
            "uploading item groups");
     // the host vectors may change on the next call
@@ -156,6 +161,9 @@ olb_status capture(olb_batch *b) {
     a.grid = b->grid;
     a.block = b->block;
     a.stream = b->stream;
+    a.walls = 0;
+    for (const Member &m : b->members)
+        if (m.lat->p.boundary == OLB_BOUNDARY_WALLS_X) a.walls = 1;
     B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
            "beginning graph capture");
     cudaError_t e = cudaSuccess;
@@ -177,6 +185,7 @@ olb_status capture(olb_batch *b) {
     b->graph = g;
     B_CUDA(cudaGraphInstantiate(&b->exec, g, 0), "instantiating batch graph");
     b->captured = true;
+    b->graph_walls = a.walls != 0;
     return OLB_OK;
 }
 
@@ -230,13 +239,13 @@ olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out) {
     b->grid = per_sm * b->num_sms;
     e = cudaMalloc(&b->d_descs, (size_t)p->max_lattices * b->desc_size);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, (size_t)p->max_items * sizeof(int4));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_groups, 9 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_groups, (NGROUPS + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_g, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_groups, 9 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_groups, (NGROUPS + 1) * sizeof(int));
     if (e != cudaSuccess) return bail(bcuda(e, "allocating batch tables"));
-    for (int q = 0; q < 9; ++q) b->h_groups[q] = 0;
+    for (int q = 0; q <= NGROUPS; ++q) b->h_groups[q] = 0;
     e = cudaMemsetAsync(b->d_g, 0, sizeof(long long), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_groups, 0, 9 * sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_groups, 0, (NGROUPS + 1) * sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bail(bcuda(e, "clearing batch tables"));
     b->G = 0;
@@ -270,6 +279,14 @@ olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps) {
         return st;
     }
     lat->batch = b;
+    if (b->captured && !b->graph_walls && lat->p.boundary == OLB_BOUNDARY_WALLS_X) {
+        // the graph lacks the wall-column kernels: capture again on the next run
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        b->captured = false;
+    }
     return OLB_OK;
 }
 

@@ -34,13 +34,15 @@ template <typename C> struct BatchDesc {
     CollConst<C> k;
 };
 
-// Work items are grouped on the host by (equilibrium, collision, parity
-// class): group = (eq * 2 + coll) * 2 + c, with c = (t_base - g_base) & 1 the
-// lattice's fixed offset between its own time and the global step, so that
-// at global step g every lattice of class c has time parity (g + c) & 1.
-// Each kernel below handles one (eq, coll) and, for the in-place layout, one
-// parity: one item body per kernel keeps register use at the single-lattice
-// kernels' level.  groups[0..8] are the item offsets of the 8 groups.
+// Work items are grouped on the host by (walls, equilibrium, collision,
+// parity class): group = ((walls * 2 + eq) * 2 + coll) * 2 + c, with
+// c = (t_base - g_base) & 1 the lattice's fixed offset between its own time
+// and the global step, so that at global step g every lattice of class c has
+// time parity (g + c) & 1.  Each kernel below handles one (walls, eq, coll)
+// and, for the in-place layout, one parity: one item body per kernel keeps
+// register use at the single-lattice kernels' level.  groups[0..16] are the
+// item offsets of the 16 groups; the bounce-back (walls) kernels are only
+// launched by batches that hold a lattice with wall columns.
 enum { BATCH_AB = 0, BATCH_AA_EVEN = 1, BATCH_AA_ODD = 2 };
 
 // 256 threads x 2 blocks per SM caps registers at 128 per thread: the
@@ -48,14 +50,14 @@ enum { BATCH_AB = 0, BATCH_AA_EVEN = 1, BATCH_AA_ODD = 2 };
 // the parameter bank, and left to itself the compiler keeps them all in
 // registers (150-180 for half storage), halving occupancy; reloading a few
 // from L1 is cheaper (measured: 49 -> 63 GLUPS on 512 mixed FP16 lattices).
-template <int S, int KIND, int EQ, int COLL>
+template <int S, int KIND, int EQ, int COLL, bool WALLS>
 __global__ void __launch_bounds__(256, 2)
     k_batch_step(const BatchDesc<typename Storage<S>::C> *__restrict__ descs,
                  const int4 *__restrict__ items, const int *__restrict__ groups,
                  const long long *__restrict__ g_round, int k) {
     using T = typename Storage<S>::T;
     const long long g = *g_round + k;
-    constexpr int combo = EQ * 2 + COLL;
+    constexpr int combo = ((WALLS ? 1 : 0) * 2 + EQ) * 2 + COLL;
     int lo, hi;
     if constexpr (KIND == BATCH_AB) {
         lo = groups[combo * 2];
@@ -76,31 +78,36 @@ __global__ void __launch_bounds__(256, 2)
         if constexpr (KIND == BATCH_AB) {
             const T *src = base + (size_t)(t & 1) * d.buf_elems;
             T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
-            item_ab<S, EQ, COLL, false>(src, dst, d.nx, d.ny, d.pitch, d.plane, it.y, it.z, lane,
-                                        d.lw, d.k, t, d.sr != 0);
+            item_ab<S, EQ, COLL, false, WALLS>(src, dst, d.nx, d.ny, d.pitch, d.plane, it.y, it.z,
+                                               lane, d.lw, d.k, t, d.sr != 0);
         } else if constexpr (KIND == BATCH_AA_ODD) {
-            item_aa_odd<S, EQ, COLL, false>(base, d.nx, d.ny, d.pitch, d.plane, it.y, it.z, lane,
-                                            d.lw, d.k, t, d.sr != 0);
+            item_aa_odd<S, EQ, COLL, false, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, it.y, it.z,
+                                                   lane, d.lw, d.k, t, d.sr != 0);
         } else {
-            item_aa_even<S, EQ, COLL, false>(base, d.nx, d.ny, d.pitch, d.plane, it.y, it.z, lane,
-                                             d.lw, d.k, t, d.sr != 0);
+            item_aa_even<S, EQ, COLL, false, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, it.y,
+                                                    it.z, lane, d.lw, d.k, t, d.sr != 0);
         }
     }
 }
 
 template <int S> struct BatchLaunchT {
-    template <int KIND>
-    static cudaError_t launch_kind(const BatchLaunch &a) {
+    template <int KIND, bool WALLS>
+    static void launch_combos(const BatchLaunch &a) {
         using D = BatchDesc<typename Storage<S>::C>;
         const D *descs = static_cast<const D *>(a.descs);
-        k_batch_step<S, KIND, EQ_GUIDED, COLL_OREG><<<a.grid, a.block, 0, a.stream>>>(
+        k_batch_step<S, KIND, EQ_GUIDED, COLL_OREG, WALLS><<<a.grid, a.block, 0, a.stream>>>(
             descs, a.items, a.groups, a.g, a.k);
-        k_batch_step<S, KIND, EQ_GUIDED, COLL_BGK><<<a.grid, a.block, 0, a.stream>>>(
+        k_batch_step<S, KIND, EQ_GUIDED, COLL_BGK, WALLS><<<a.grid, a.block, 0, a.stream>>>(
             descs, a.items, a.groups, a.g, a.k);
-        k_batch_step<S, KIND, EQ_POLY2, COLL_OREG><<<a.grid, a.block, 0, a.stream>>>(
+        k_batch_step<S, KIND, EQ_POLY2, COLL_OREG, WALLS><<<a.grid, a.block, 0, a.stream>>>(
             descs, a.items, a.groups, a.g, a.k);
-        k_batch_step<S, KIND, EQ_POLY2, COLL_BGK><<<a.grid, a.block, 0, a.stream>>>(
+        k_batch_step<S, KIND, EQ_POLY2, COLL_BGK, WALLS><<<a.grid, a.block, 0, a.stream>>>(
             descs, a.items, a.groups, a.g, a.k);
+    }
+    template <int KIND>
+    static cudaError_t launch_kind(const BatchLaunch &a) {
+        launch_combos<KIND, false>(a);
+        if (a.walls) launch_combos<KIND, true>(a);
         return cudaGetLastError();
     }
     static cudaError_t launch(const BatchLaunch &a) {
@@ -113,9 +120,9 @@ template <int S> struct BatchLaunchT {
         int n = 0;
         cudaError_t e = layout == 0
             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                  &n, k_batch_step<S, BATCH_AB, EQ_GUIDED, COLL_OREG>, block, 0)
+                  &n, k_batch_step<S, BATCH_AB, EQ_GUIDED, COLL_OREG, false>, block, 0)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                  &n, k_batch_step<S, BATCH_AA_ODD, EQ_GUIDED, COLL_OREG>, block, 0);
+                  &n, k_batch_step<S, BATCH_AA_ODD, EQ_GUIDED, COLL_OREG, false>, block, 0);
         return e == cudaSuccess ? n : 0;
     }
 };

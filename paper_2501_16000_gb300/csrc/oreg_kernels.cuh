@@ -149,8 +149,53 @@ __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<
     }
 }
 
+// Full-way bounce-back walls at columns 0 and nx - 1 (WALLS kernels only): a
+// wall node does not collide; it returns every population along the link it
+// arrived on, post_i(x) = f_opp(i)(x), with f the pre-collision state S_t.
+// Called after collide_vec for lanes that hold a wall node, it reads the wall
+// node's pre-collision values again from memory, which no thread has
+// modified yet in any layout: A-B reads the unchanged source buffer; in the
+// AA layout each location is read and written by its own node's update only,
+// and this node's stores (including pushes by neighbouring lanes, whose
+// values come from this lane through shuffles) come later.  MODE selects the
+// addressing of f_k(x): A-B source plane k at x - c_k; AA even plane k at x;
+// AA odd plane opp(k) at x - c_k.  The values are exact decodes of stored
+// elements, so re-encoding them (also stochastically) returns the same bits.
+template <int S, int MODE>
+__device__ __forceinline__ void bounce_back_walls(const typename Storage<S>::T *base, size_t plane,
+                                                  int pitch, int y, int ny, int xb, int nx,
+                                                  typename Storage<S>::C f[9][Storage<S>::V]) {
+    using ST = Storage<S>;
+#pragma unroll
+    for (int j = 0; j < ST::V; ++j) {
+        const int x = xb + j;
+        if (x == 0 || x == nx - 1) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int k = opp_of(i);
+                size_t at;
+                if (MODE == STATE_AA_EVEN) {
+                    at = k * plane + (size_t)y * pitch + x;
+                } else {
+                    int xs = x - cx_of(k);
+                    xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+                    const int p = MODE == STATE_AA_ODD ? opp_of(k) : k;
+                    at = p * plane + (size_t)wrap_row(y - cy_of(k), ny) * pitch + xs;
+                }
+                f[i][j] = ST::dec(base[at]);
+            }
+        }
+    }
+}
+
+// Whether the lane's nodes xb .. xb+V-1 include a wall column.
+template <int S>
+__device__ __forceinline__ bool lane_has_wall(int xb, int nx) {
+    return xb < nx && (xb == 0 || xb + Storage<S>::V > nx - 1);
+}
+
 // One warp work item: row y, segment seg (32*V nodes) of a lattice.
-template <int S, int EQ, int COLL, bool COMP>
+template <int S, int EQ, int COLL, bool COMP, bool WALLS>
 __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict__ src,
                                         typename Storage<S>::T *__restrict__ dst, int nx, int ny,
                                         int pitch, size_t plane, int y0, int seg, int lane, int lw,
@@ -171,6 +216,10 @@ __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict
     pull_all<S, false>(src, plane, pitch, y, ny, xb, nx, sub, W, f);
 
     collide_vec<S, EQ, COLL, COMP>(f, k);
+    if constexpr (WALLS) {
+        if (lane_has_wall<S>(xb, nx))
+            bounce_back_walls<S, STATE_AB>(src, plane, pitch, y, ny, xb, nx, f);
+    }
 
     if (xb < nx) {
         if (xb + V > nx) zero_padding<S>(f, xb, nx);
@@ -187,7 +236,7 @@ __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict
     }
 }
 
-template <int S, int EQ, int COLL, bool COMP>
+template <int S, int EQ, int COLL, bool COMP, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *__restrict__ src,
                                                  typename Storage<S>::T *__restrict__ dst, int nx,
                                                  int ny, int pitch, size_t plane, int segs,
@@ -196,8 +245,9 @@ __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *_
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
     if (item >= (long long)groups * segs) return;  // warp-uniform
-    item_ab<S, EQ, COLL, COMP>(src, dst, nx, ny, pitch, plane, (int)(item / segs) << (5 - lw),
-                               (int)(item % segs), threadIdx.x & 31, lw, k, t, sr);
+    item_ab<S, EQ, COLL, COMP, WALLS>(src, dst, nx, ny, pitch, plane,
+                                      (int)(item / segs) << (5 - lw), (int)(item % segs),
+                                      threadIdx.x & 31, lw, k, t, sr);
 }
 
 // ---------------------------------------------------------------------------
@@ -207,7 +257,7 @@ __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *_
 // Every memory location is read and then written by the same node's update
 // only, so the update is race-free in place.
 // ---------------------------------------------------------------------------
-template <int S, int EQ, int COLL, bool COMP>
+template <int S, int EQ, int COLL, bool COMP, bool WALLS>
 __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, int ny, int pitch,
                                              size_t plane, int y0, int seg, int lane, int lw,
                                              const CollConst<typename Storage<S>::C> &k,
@@ -232,6 +282,10 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
         for (int j = 0; j < V; ++j) f[i][j] = ST::dec(v.e[j]);
     }
     collide_vec<S, EQ, COLL, COMP>(f, k);
+    if constexpr (WALLS) {
+        if (lane_has_wall<S>(xb, nx))
+            bounce_back_walls<S, STATE_AA_EVEN>(A, plane, pitch, y, ny, xb, nx, f);
+    }
     if (xb + V > nx) zero_padding<S>(f, xb, nx);
     typename ST::T e[9][V];
     encode_vec<S>(f, e, xb, y, t, sr);
@@ -244,7 +298,7 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
     }
 }
 
-template <int S, int EQ, int COLL, bool COMP>
+template <int S, int EQ, int COLL, bool COMP, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A, int nx, int ny,
                                                       int pitch, size_t plane, int segs, int lw,
                                                       const CollConst<typename Storage<S>::C> k,
@@ -252,8 +306,9 @@ __global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A,
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
     if (item >= (long long)groups * segs) return;
-    item_aa_even<S, EQ, COLL, COMP>(A, nx, ny, pitch, plane, (int)(item / segs) << (5 - lw),
-                                    (int)(item % segs), threadIdx.x & 31, lw, k, t, sr);
+    item_aa_even<S, EQ, COLL, COMP, WALLS>(A, nx, ny, pitch, plane,
+                                           (int)(item / segs) << (5 - lw), (int)(item % segs),
+                                           threadIdx.x & 31, lw, k, t, sr);
 }
 
 template <int S, int I>
@@ -264,7 +319,7 @@ __device__ __forceinline__ void push_plane(typename Storage<S>::T *A, size_t pla
     store_row_shifted_raw<S, cx_of(I)>(A + I * plane + (size_t)yd * pitch, xb, nx, sub, W, p);
 }
 
-template <int S, int EQ, int COLL, bool COMP>
+template <int S, int EQ, int COLL, bool COMP, bool WALLS>
 __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, int ny, int pitch,
                                             size_t plane, int y0, int seg, int lane, int lw,
                                             const CollConst<typename Storage<S>::C> &k,
@@ -284,6 +339,10 @@ __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, i
     pull_all<S, true>(A, plane, pitch, y, ny, xb, nx, sub, W, f);
 
     collide_vec<S, EQ, COLL, COMP>(f, k);
+    if constexpr (WALLS) {
+        if (lane_has_wall<S>(xb, nx))
+            bounce_back_walls<S, STATE_AA_ODD>(A, plane, pitch, y, ny, xb, nx, f);
+    }
     if (xb < nx && xb + V > nx) zero_padding<S>(f, xb, nx);
     typename ST::T e[9][V];
     encode_vec<S>(f, e, xb, y, t, sr);
@@ -299,7 +358,7 @@ __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, i
     push_plane<S, 8>(A, plane, pitch, y, ny, xb, nx, sub, W, e[8]);
 }
 
-template <int S, int EQ, int COLL, bool COMP>
+template <int S, int EQ, int COLL, bool COMP, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
                                                      int pitch, size_t plane, int segs, int lw,
                                                      const CollConst<typename Storage<S>::C> k,
@@ -307,8 +366,9 @@ __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, 
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
     if (item >= (long long)groups * segs) return;
-    item_aa_odd<S, EQ, COLL, COMP>(A, nx, ny, pitch, plane, (int)(item / segs) << (5 - lw),
-                                   (int)(item % segs), threadIdx.x & 31, lw, k, t, sr);
+    item_aa_odd<S, EQ, COLL, COMP, WALLS>(A, nx, ny, pitch, plane,
+                                          (int)(item / segs) << (5 - lw), (int)(item % segs),
+                                          threadIdx.x & 31, lw, k, t, sr);
 }
 
 // ---------------------------------------------------------------------------
@@ -319,34 +379,46 @@ template <int S> struct StepLaunch {
     using T = typename ST::T;
     using C = typename ST::C;
 
-    template <int EQ, int COLL, bool COMP>
+    template <int EQ, int COLL, bool COMP, bool WALLS>
     static void step_eq(const StepArgs &a, dim3 grid, dim3 block) {
         const CollConst<C> &k = *static_cast<const CollConst<C> *>(a.kconst);
         const int segs = a.segs;
         if (a.layout == 0) {
-            k_step_ab<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
+            k_step_ab<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
                 static_cast<const T *>(a.src), static_cast<T *>(a.dst), a.nx, a.ny, a.pitch,
                 a.plane, segs, a.lw, k, a.t, a.sr != 0);
         } else if (a.parity == 0) {
-            k_step_aa_even<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
+            k_step_aa_even<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
                 static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
                 a.sr != 0);
         } else {
-            k_step_aa_odd<S, EQ, COLL, COMP><<<grid, block, 0, a.stream>>>(
+            k_step_aa_odd<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
                 static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
                 a.sr != 0);
         }
     }
 
-    template <bool COMP>
+    template <bool COMP, bool WALLS>
     static void step_comp(const StepArgs &a, dim3 grid, dim3 block) {
         if (a.eq == EQ_GUIDED) {
-            if (a.coll == COLL_OREG) step_eq<EQ_GUIDED, COLL_OREG, COMP>(a, grid, block);
-            else step_eq<EQ_GUIDED, COLL_BGK, COMP>(a, grid, block);
+            if (a.coll == COLL_OREG) step_eq<EQ_GUIDED, COLL_OREG, COMP, WALLS>(a, grid, block);
+            else step_eq<EQ_GUIDED, COLL_BGK, COMP, WALLS>(a, grid, block);
         } else {
-            if (a.coll == COLL_OREG) step_eq<EQ_POLY2, COLL_OREG, COMP>(a, grid, block);
-            else step_eq<EQ_POLY2, COLL_BGK, COMP>(a, grid, block);
+            if (a.coll == COLL_OREG) step_eq<EQ_POLY2, COLL_OREG, COMP, WALLS>(a, grid, block);
+            else step_eq<EQ_POLY2, COLL_BGK, COMP, WALLS>(a, grid, block);
         }
+    }
+
+    template <bool WALLS>
+    static void step_walls(const StepArgs &a, dim3 grid, dim3 block) {
+        // compensated sums exist for FP32 storage only
+        if constexpr (S == ST_F32) {
+            if (a.comp) {
+                step_comp<true, WALLS>(a, grid, block);
+                return;
+            }
+        }
+        step_comp<false, WALLS>(a, grid, block);
     }
 
     static cudaError_t step(const StepArgs &a) {
@@ -355,11 +427,10 @@ template <int S> struct StepLaunch {
         const long long items = groups * a.segs;
         dim3 block(32 * warps);
         dim3 grid((unsigned)((items + warps - 1) / warps));
-        if (a.comp && S == ST_F32) step_comp<true>(a, grid, block);
-        else step_comp<false>(a, grid, block);
+        if (a.walls) step_walls<true>(a, grid, block);
+        else step_walls<false>(a, grid, block);
         return cudaGetLastError();
     }
-
 };
 
 }  // namespace oreg

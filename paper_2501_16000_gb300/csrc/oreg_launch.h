@@ -31,6 +31,7 @@ struct StepArgs {
     int eq, coll, layout, parity;
     int comp;          // compensated conserved-moment sums (FP32 only)
     int sr;            // stochastic rounding (half formats only)
+    int walls;         // full-way bounce-back wall columns x = 0 and x = nx - 1
     long long t;       // time of the state being advanced
     int warps_per_block;
     const void *kconst;  // CollConst<C> of the storage's compute type
@@ -53,6 +54,10 @@ struct InitSpec {
     double rho_a, rho_b;  // shear: rho0; shock: left/right density
     double u0, ex, ey;    // shear amplitude and direction e_perp
     int m, n;             // shear wave vector integers
+    double ux_mean, uy_mean;  // shear: uniform mean flow
+    int first_order;          // shear: add f^(1) of Eq. 5 from the analytic gradient
+    double kx, ky;            // shear: wave vector 2 pi (m/nx, n/ny)
+    double tau;               // relaxation time entering Eq. 5
     int x_split;          // shock split column
     const double *rho, *ux, *uy;  // fields mode: device arrays [rows][nx]
     int y0, rows;                 // rows initialised by this launch
@@ -91,10 +96,11 @@ OREG_DECLARE_LAUNCHERS(bf16)
 struct BatchLaunch {
     const void *descs;        // BatchDesc<C>[]
     const int4 *items;        // work items (descriptor, first row, segment), grouped
-    const int *groups;        // device: item offsets of the 8 groups (9 entries)
+    const int *groups;        // device: item offsets of the 16 groups (17 entries)
     const long long *g;       // device: global step counter of this round
     int k;                    // step within the round
     int layout;
+    int walls;                // also launch the bounce-back (wall column) kernels
     int grid, block;
     cudaStream_t stream;
 };
@@ -110,6 +116,6 @@ OREG_DECLARE_BATCH_LAUNCHERS(f16)
 OREG_DECLARE_BATCH_LAUNCHERS(bf16)
 
 constexpr int RED_BLOCKS_MAX = 1216;  // fixed reduction grid (8 x 152 SMs)
-constexpr int RED_QUANTITIES = 5;
+constexpr int RED_QUANTITIES = 6;
 
 }  // namespace oreg

@@ -29,10 +29,11 @@ def _dptr(a: np.ndarray):
 
 
 def make_params(nx, ny, tau, theta=1.0 / 3.0, eq="guided", coll="oreg", storage="f32",
-                layout="ab", rho0=1.0, device_buffer=0, buffer_bytes=0, stream=0):
+                layout="ab", rho0=1.0, device_buffer=0, buffer_bytes=0, stream=0,
+                boundary="periodic"):
     return B.olb_params(int(nx), int(ny), float(tau), float(theta), float(rho0), EQ[eq],
                         COLL[coll], STORAGE[storage], LAYOUT[layout], device_buffer or None,
-                        int(buffer_bytes), stream or None)
+                        int(buffer_bytes), stream or None, B.BOUNDARY[boundary])
 
 
 def required_bytes(**kw) -> int:
@@ -41,20 +42,23 @@ def required_bytes(**kw) -> int:
 
 
 class Lattice:
-    """One periodic D2Q9 lattice advanced by the OReg (or BGK) update.
+    """One D2Q9 lattice (periodic, or with bounce-back wall columns at x = 0
+    and x = nx - 1) advanced by the OReg (or BGK) update.
 
     ``torch_memory=True`` places the populations in a torch CUDA tensor and
     runs on torch's current stream (the default when torch sees a GPU)."""
 
     def __init__(self, nx, ny, tau, theta=1.0 / 3.0, eq="guided", coll="oreg",
-                 storage="f32", layout="ab", rho0=1.0, torch_memory=None, stream=None):
+                 storage="f32", layout="ab", rho0=1.0, torch_memory=None, stream=None,
+                 boundary="periodic"):
         self.nx, self.ny, self.tau, self.theta = int(nx), int(ny), float(tau), float(theta)
         self.eq, self.coll, self.storage, self.layout = eq, coll, storage, layout
+        self.boundary = boundary
         self._buf = None
         self._handle = None
         self.stream = None  # torch stream the lattice runs on (torch memory only)
         kw = dict(nx=nx, ny=ny, tau=tau, theta=theta, eq=eq, coll=coll, storage=storage,
-                  layout=layout, rho0=rho0)
+                  layout=layout, rho0=rho0, boundary=boundary)
         dev_ptr, nbytes, sptr = 0, 0, 0
         if torch_memory is None:
             try:
@@ -129,6 +133,12 @@ class Lattice:
     def init_shear_wave(self, rho0=1.0, u0=0.05, m=1, n=0) -> None:
         B.call("olb_init_shear_wave", self.handle, float(rho0), float(u0), int(m), int(n))
 
+    def init_shear_flow(self, rho0=1.0, u0=0.05, m=1, n=0, ux_mean=0.0, uy_mean=0.0,
+                        first_order=False) -> None:
+        """Shear wave on a uniform mean flow; ``first_order`` adds f^(1) of Eq. 5."""
+        B.call("olb_init_shear_flow", self.handle, float(rho0), float(u0), int(m), int(n),
+               float(ux_mean), float(uy_mean), 1 if first_order else 0)
+
     def init_shock_tube(self, rho_left=1.5, rho_right=0.75, x_split=None) -> None:
         xs = self.nx // 2 if x_split is None else int(x_split)
         B.call("olb_init_shock_tube", self.handle, float(rho_left), float(rho_right), xs)
@@ -142,7 +152,11 @@ class Lattice:
     def init_case(self, case) -> None:
         """Initial condition of a ``workloads.LatticeCase``."""
         if case.case == "shear":
-            self.init_shear_wave(case.rho0, case.u0, case.m, case.n)
+            if case.ux_mean or case.uy_mean or case.first_order:
+                self.init_shear_flow(case.rho0, case.u0, case.m, case.n, case.ux_mean,
+                                     case.uy_mean, case.first_order)
+            else:
+                self.init_shear_wave(case.rho0, case.u0, case.m, case.n)
         else:
             self.init_shock_tube(case.rho_left, case.rho_right, case.x_split)
 
@@ -185,3 +199,9 @@ class Lattice:
         a = ctypes.c_double()
         B.call("olb_wave_amplitude", self.handle, int(m), int(n), ctypes.byref(a))
         return a.value
+
+    def wave_mode(self, m: int, n: int) -> tuple[float, float]:
+        """(a_sin, a_cos): both quadratures of the shear-mode projection."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        B.call("olb_wave_mode", self.handle, int(m), int(n), ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
