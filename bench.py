@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--layout", default="ab", choices=["ab", "aa"])
     ap.add_argument("--comp", type=int, default=0, help="OLB_OPT_COMPENSATED (FP32)")
     ap.add_argument("--warps", type=int, default=4, help="OLB_OPT_WARPS_PER_BLOCK")
+    ap.add_argument("--sr", type=int, default=None,
+                    help="OLB_OPT_STOCHASTIC_ROUNDING for f16/bf16 (library default: 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extended", action="store_true",
                     help="skip the batched, serving and precision sections")
@@ -269,6 +271,8 @@ def run_native(args):
                   args.layout, stream=stream)
     lat.set_option(B.OLB_OPT_COMPENSATED, args.comp)
     lat.set_option(B.OLB_OPT_WARPS_PER_BLOCK, args.warps)
+    if args.sr is not None:
+        lat.set_option(B.OLB_OPT_STOCHASTIC_ROUNDING, args.sr)
     lat.init_case(case)
 
     def barrier():
@@ -364,6 +368,8 @@ def run_native(args):
                        "wave": [case.m, case.n], "storage": args.storage,
                        "layout": args.layout, "diagnostics_every": DIAG_EVERY,
                        "compensated": args.comp, "warps_per_block": args.warps,
+                       "stochastic_rounding": (args.sr if args.sr is not None else
+                                               int(args.storage in ("f16", "bf16"))),
                        "l2": f"inputs larger than L2 ({lat_bytes(args.storage, N) / 1e9:.1f} GB "
                              f"state vs 126 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

@@ -143,6 +143,15 @@ CollConst<C> make_const(const olb_params *p) {
     return k;
 }
 
+// FP32 constants of the stream-collide kernels, in the storage format's step
+// units (populations, rho0, shifts and corrections times STEP_SCALE, a power
+// of two; see Storage in oreg_device.cuh).
+CollConst<float> make_step_const_f32(const olb_params *p) {
+    olb_params q = *p;
+    if (p->storage == OLB_F16_SHIFTED) q.rho0 *= Storage<ST_F16>::STEP_SCALE;
+    return make_const<float>(&q);
+}
+
 // FP64 constants (initialisation and readback) whose shift is exactly the
 // stored format's shift.
 CollConst<double> make_const_f64_for(const olb_params *p) {
@@ -317,7 +326,7 @@ olb_status olb_create_lattice(const olb_params *p, olb_lattice **out) {
     L->sr = (p->storage == OLB_F16_SHIFTED || p->storage == OLB_BF16_SHIFTED) ? 1 : 0;
     L->warps_per_block = 4;
     L->kd = make_const_f64_for(p);
-    L->kf = make_const<float>(p);
+    L->kf = make_step_const_f32(p);
 
     auto bail = [&](olb_status s) {
         olb_destroy(L);

@@ -14,6 +14,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace oreg {
 
 // ---------------------------------------------------------------------------
@@ -47,41 +49,81 @@ enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 // Storage traits: T = stored element, C = compute type, V = elements per 16 B.
 // ---------------------------------------------------------------------------
 template <int S> struct Storage;
+//
+// dec/enc map stored elements to and from g = f - s (used by the auxiliary
+// kernels with the FP64 constants).  The stream-collide kernels use
+// dec_step/enc_step (and the packed enc2/enc2_stochastic of the half
+// formats), which work in step units: g * STEP_SCALE.  The collision is
+// homogeneous of degree one in (f, rho) (f^eq is linear in rho and f^OReg
+// scales as f^eq S / rho), so the step kernels run it unchanged in units
+// scaled by a power of two, with rho0, the shifts and their corrections
+// scaled alike on the host; scaling by a power of two is exact, so this
+// only removes two multiplications per element.
 template <> struct Storage<ST_F64> {
     using T = double; using C = double; static constexpr int V = 2;
+    static constexpr double STEP_SCALE = 1.0;
     __device__ static C dec(T v) { return v; }
     __device__ static T enc(C v) { return v; }
+    __device__ static C dec_step(T v) { return v; }
+    __device__ static T enc_step(C v) { return v; }
 };
 template <> struct Storage<ST_F32> {
     using T = float; using C = float; static constexpr int V = 4;
+    static constexpr double STEP_SCALE = 1.0;
     __device__ static C dec(T v) { return v; }
     __device__ static T enc(C v) { return v; }
+    __device__ static C dec_step(T v) { return v; }
+    __device__ static T enc_step(C v) { return v; }
 };
-// Half formats also offer stochastic rounding: r is 16 uniform random bits;
-// the bits of v below the format's last mantissa bit (13 for f16, 16 for
-// bf16) get r added before truncation, so v rounds away from zero with
-// probability equal to its distance from the truncated value (exact for
-// normal numbers; values in the f16 subnormal range keep a bias below one
-// subnormal step).
+// Half formats also offer stochastic rounding: the bits of v below the
+// format's last mantissa bit (13 for f16, 16 for bf16) get uniform random
+// bits added before truncation, so v rounds away from zero with probability
+// equal to its distance from the truncated value.
 // f16 stores g * 2^8: the shifted populations are small (|g| ~ 1e-5 .. 1e-1
 // in the benchmarks), and the scale keeps them above the f16 subnormal
 // range (2^-14), where the format has fixed absolute resolution 2^-24.
 // Scaling by a power of two is exact.  |g| must stay below 65504 / 2^8 = 255.
+//
+// Pairs of adjacent elements are encoded with one packed conversion:
+// enc2 (round to nearest even) and enc2_stochastic, the sm_100-family
+// stochastic-rounding conversion cvt.rs.{f16x2,bf16x2}.f32, which adds the
+// low 13 (f16) or all 16 (bf16) bits of each 16-bit half of r to the
+// discarded mantissa bits of the matching input (low half -> lo, high half
+// -> hi) and truncates.  The result packs lo in the low and hi in the high
+// 16 bits, the order in which the two elements sit in memory.
 template <> struct Storage<ST_F16> {
     using T = __half; using C = float; static constexpr int V = 8;
     static constexpr float SCALE = 256.0f, INV_SCALE = 1.0f / 256.0f;
+    static constexpr double STEP_SCALE = 256.0;  // step units are the stored units
     __device__ static C dec(T v) { return __half2float(v) * INV_SCALE; }
     __device__ static T enc(C v) { return __float2half_rn(v * SCALE); }
-    __device__ static T enc_stochastic(C v, uint32_t r) {
-        return __float2half_rz(__uint_as_float(__float_as_uint(v * SCALE) + (r & 0x1FFFu)));
+    __device__ static C dec_step(T v) { return __half2float(v); }
+    __device__ static T enc_step(C v) { return __float2half_rn(v); }
+    __device__ static uint32_t enc2(C lo, C hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    __device__ static uint32_t enc2_stochastic(C lo, C hi, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
     }
 };
 template <> struct Storage<ST_BF16> {
     using T = __nv_bfloat16; using C = float; static constexpr int V = 8;
+    static constexpr double STEP_SCALE = 1.0;
     __device__ static C dec(T v) { return __bfloat162float(v); }
     __device__ static T enc(C v) { return __float2bfloat16_rn(v); }
-    __device__ static T enc_stochastic(C v, uint32_t r) {
-        return __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r & 0xFFFFu)));
+    __device__ static C dec_step(T v) { return __bfloat162float(v); }
+    __device__ static T enc_step(C v) { return __float2bfloat16_rn(v); }
+    __device__ static uint32_t enc2(C lo, C hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    __device__ static uint32_t enc2_stochastic(C lo, C hi, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
     }
 };
 
@@ -101,10 +143,19 @@ __device__ __forceinline__ uint32_t node_seed(int x, int y, long long t) {
     h ^= h >> 16;
     return h;
 }
-__device__ __forceinline__ uint32_t direction_bits(uint32_t h, int i) {
+__device__ __forceinline__ uint32_t direction_mult(int i) {
     const uint32_t m[9] = {0x9E3779B9u, 0x7F4A7C15u, 0xF39CC061u, 0x5851F42Du, 0xC8E2D8F5u,
                            0x2545F491u, 0xB5297A4Du, 0x68E31DA5u, 0x1B56C4E9u};
-    return (h * m[i]) >> 16;
+    return m[i];
+}
+__device__ __forceinline__ uint32_t direction_bits(uint32_t h, int i) {
+    return (h * direction_mult(i)) >> 16;
+}
+// The draws of direction i for two nodes in one word: direction_bits(h_lo, i)
+// in the low and direction_bits(h_hi, i) in the high 16 bits (the upper
+// halves of the two products, gathered by one byte permutation).
+__device__ __forceinline__ uint32_t direction_bits2(uint32_t h_lo, uint32_t h_hi, int i) {
+    return __byte_perm(h_lo * direction_mult(i), h_hi * direction_mult(i), 0x7632);
 }
 
 // 16-byte vector of V stored elements.
@@ -195,13 +246,16 @@ __device__ __forceinline__ F2 operator*(F2 a, F2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
     return d;
 }
-__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2(a.lo() / b.lo(), a.hi() / b.hi()); }
 __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) {
     F2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
     return d;
 }
 using ::fma;  // keep the scalar overloads visible next to the packed one
+
+// Per-lane IEEE division (the packed reciprocal estimate plus a Newton step
+// measured 15% slower in the half-format kernels).
+__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2(a.lo() / b.lo(), a.hi() / b.hi()); }
 
 // Error-free sum: a + b = s + e exactly (Knuth TwoSum).
 template <typename C>
@@ -265,8 +319,24 @@ __device__ __forceinline__ void conserved(const C g[9], const CollConst<C> &k, C
 // BGK (Eq. 1): post = geq + (1 - 1/tau) (g - geq).
 template <int EQ, int COLL, typename C, bool COMP>
 __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst<C> &k) {
-    C drho, jx, jy;
-    conserved<C, COMP>(g, k, drho, jx, jy);
+    // Packed pairs (issue-bound half formats) share the opposite-direction
+    // sums between the conserved moments and the stress and fold the OReg
+    // prefactor into the stress; float and double keep the plain order.
+    constexpr bool PACKED = std::is_same<C, F2>::value;
+    C drho, jx, jy, dxy, pxy;
+    if constexpr (PACKED && !COMP) {
+        const C s13 = g[1] + g[3], s24 = g[2] + g[4], s57 = g[5] + g[7], s68 = g[6] + g[8];
+        const C d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d68 = g[6] - g[8];
+        drho = (((g[0] + s13) + (s24 + s57)) + s68) - k.sum_corr;
+        jx = (d13 + d57) - d68;
+        jy = (d24 + d57) + d68;
+        dxy = s13 - s24;
+        pxy = s57 - s68;
+    } else {
+        conserved<C, COMP>(g, k, drho, jx, jy);
+        dxy = (g[1] + g[3]) - (g[2] + g[4]);
+        pxy = (g[5] + g[7]) - (g[6] + g[8]);
+    }
     const C rho = k.rho0 + drho;
     const C inv_rho = C(1) / rho;
     const C ux = jx * inv_rho, uy = jy * inv_rho;
@@ -311,20 +381,29 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
 #pragma unroll
         for (int i = 0; i < 9; ++i) post[i] = fma(k.lam, g[i] - geq[i], geq[i]);
     } else {
-        const C dxy = (g[1] + g[3]) - (g[2] + g[4]);
-        const C pxy = (g[5] + g[7]) - (g[6] + g[8]);
         const C sxx = C(0.5) * (dxy - rho * (ux2 - uy2));
         const C sxy = pxy - rho * ux * uy;
         const C a = k.lam * k.inv_2th2 * inv_rho;
         const C X[3] = {-ux, C(1) - ux, C(-1) - ux};
         const C Y[3] = {-uy, C(1) - uy, C(-1) - uy};
-        const C two_sxy = C(2) * sxy;
+        if constexpr (PACKED) {
+            const C asxx = a * sxx, a2sxy = C(2) * a * sxy;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int ia = kidx(cx_of(i)), ib = kidx(cy_of(i));
-            const C d = fma(X[ia] * X[ia] - Y[ib] * Y[ib], sxx, X[ia] * Y[ib] * two_sxy);
-            const C feq = k.shift[dcls(i)] + geq[i];
-            post[i] = fma(feq, a * d, geq[i]);
+            for (int i = 0; i < 9; ++i) {
+                const int ia = kidx(cx_of(i)), ib = kidx(cy_of(i));
+                const C ad = fma(X[ia] * X[ia] - Y[ib] * Y[ib], asxx, X[ia] * Y[ib] * a2sxy);
+                const C feq = k.shift[dcls(i)] + geq[i];
+                post[i] = fma(feq, ad, geq[i]);
+            }
+        } else {
+            const C two_sxy = C(2) * sxy;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int ia = kidx(cx_of(i)), ib = kidx(cy_of(i));
+                const C d = fma(X[ia] * X[ia] - Y[ib] * Y[ib], sxx, X[ia] * Y[ib] * two_sxy);
+                const C feq = k.shift[dcls(i)] + geq[i];
+                post[i] = fma(feq, a * d, geq[i]);
+            }
         }
     }
 }
@@ -382,22 +461,22 @@ __device__ __forceinline__ void shift_row(const RawRow<S> &r, int xb, int nx, in
     constexpr int V = ST::V;
     C a[V];
 #pragma unroll
-    for (int j = 0; j < V; ++j) a[j] = ST::dec(r.v.e[j]);
+    for (int j = 0; j < V; ++j) a[j] = ST::dec_step(r.v.e[j]);
     if constexpr (CX == 0) {
 #pragma unroll
         for (int j = 0; j < V; ++j) out[j] = a[j];
     } else if constexpr (CX == 1) {
         // left neighbour of the lane's first node
         C left = __shfl_up_sync(0xffffffffu, a[V - 1], 1, W);
-        if (xb < nx && (sub == 0 || xb == 0)) left = ST::dec(r.halo);
+        if (xb < nx && (sub == 0 || xb == 0)) left = ST::dec_step(r.halo);
         out[0] = left;
 #pragma unroll
         for (int j = 1; j < V; ++j) out[j] = a[j - 1];
     } else {
         // right neighbour of the lane's last node; node nx-1 wraps to x = 0
         C right = __shfl_down_sync(0xffffffffu, a[0], 1, W);
-        if (xb < nx && sub == W - 1 && xb + V < nx) right = ST::dec(r.halo);
-        const C wrapv = ST::dec(r.wrap);
+        if (xb < nx && sub == W - 1 && xb + V < nx) right = ST::dec_step(r.halo);
+        const C wrapv = ST::dec_step(r.wrap);
 #pragma unroll
         for (int j = 0; j < V - 1; ++j) out[j] = a[j + 1];
         out[V - 1] = right;

@@ -69,26 +69,45 @@ __device__ __forceinline__ void zero_padding(typename Storage<S>::C f[9][Storage
 // Encodes the post-collision values to the storage format: round to nearest,
 // or (half formats, sr) stochastically with counter-based bits per node,
 // time step and direction.
+// Half formats encode node pairs (j, j+1) with one packed conversion; the
+// stochastic draw of node x, direction i is direction_bits(node_seed(x, y, t), i).
 template <int S>
 __device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Storage<S>::V],
                                            typename Storage<S>::T e[9][Storage<S>::V], int xb,
                                            int y, long long t, bool sr) {
     using ST = Storage<S>;
+    using T = typename ST::T;
     if constexpr (S == ST_F16 || S == ST_BF16) {
+        uint32_t w[9][ST::V / 2];
         if (sr) {
 #pragma unroll
-            for (int j = 0; j < ST::V; ++j) {
-                const uint32_t h = node_seed(xb + j, y, t);
+            for (int j = 0; j < ST::V; j += 2) {
+                const uint32_t h0 = node_seed(xb + j, y, t), h1 = node_seed(xb + j + 1, y, t);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) e[i][j] = ST::enc_stochastic(f[i][j], direction_bits(h, i));
+                for (int i = 0; i < 9; ++i)
+                    w[i][j / 2] = ST::enc2_stochastic(f[i][j], f[i][j + 1], direction_bits2(h0, h1, i));
             }
-            return;
+        } else {
+#pragma unroll
+            for (int j = 0; j < ST::V; j += 2)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) w[i][j / 2] = ST::enc2(f[i][j], f[i][j + 1]);
         }
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int j = 0; j < ST::V; j += 2) {
+                const unsigned short lo = (unsigned short)(w[i][j / 2] & 0xFFFFu);
+                const unsigned short hi = (unsigned short)(w[i][j / 2] >> 16);
+                e[i][j] = *reinterpret_cast<const T *>(&lo);
+                e[i][j + 1] = *reinterpret_cast<const T *>(&hi);
+            }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int j = 0; j < ST::V; ++j) e[i][j] = ST::enc_step(f[i][j]);
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-#pragma unroll
-        for (int j = 0; j < ST::V; ++j) e[i][j] = ST::enc(f[i][j]);
 }
 
 // The collision constants broadcast to both lanes of a packed pair.
@@ -182,7 +201,7 @@ __device__ __forceinline__ void bounce_back_walls(const typename Storage<S>::T *
                     const int p = MODE == STATE_AA_ODD ? opp_of(k) : k;
                     at = p * plane + (size_t)wrap_row(y - cy_of(k), ny) * pitch + xs;
                 }
-                f[i][j] = ST::dec(base[at]);
+                f[i][j] = ST::dec_step(base[at]);
             }
         }
     }
@@ -279,7 +298,7 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
     for (int i = 0; i < 9; ++i) {
         Vec<S> v = ld_vec<S>(row + i * plane);
 #pragma unroll
-        for (int j = 0; j < V; ++j) f[i][j] = ST::dec(v.e[j]);
+        for (int j = 0; j < V; ++j) f[i][j] = ST::dec_step(v.e[j]);
     }
     collide_vec<S, EQ, COLL, COMP>(f, k);
     if constexpr (WALLS) {
