@@ -127,11 +127,13 @@ template <> struct Storage<ST_BF16> {
     }
 };
 
-// Counter-based random bits for stochastic rounding: a hash of the node and
-// time step (the 32-bit finalizer of MurmurHash3), then one multiplicative
-// hash per direction, (h * M_i) >> 16 with distinct odd M_i, whose upper
-// bits are well mixed.  The draws depend only on (x, y, t, i), so results do
-// not depend on how nodes are scheduled, batched or laid out.
+// Counter-based random bits for stochastic rounding: one hash per node pair
+// (x, x+1), x even, and time step (the 32-bit finalizer of MurmurHash3 of
+// (x/2, y, t)), then one multiplicative hash per direction, r = h * M_i with
+// distinct odd M_i, folded as r ^ (r >> 16) so that both 16-bit halves
+// (the low half feeds node x, the high half node x+1) depend on every bit of
+// h.  The draws depend only on (x, y, t, i), so results do not depend on how
+// nodes are scheduled, batched or laid out.
 __device__ __forceinline__ uint32_t node_seed(int x, int y, long long t) {
     uint32_t h = (uint32_t)x * 0x9E3779B1u;
     h ^= (uint32_t)y * 0x85EBCA77u + 0x632BE5ABu;
@@ -148,14 +150,9 @@ __device__ __forceinline__ uint32_t direction_mult(int i) {
                            0x2545F491u, 0xB5297A4Du, 0x68E31DA5u, 0x1B56C4E9u};
     return m[i];
 }
-__device__ __forceinline__ uint32_t direction_bits(uint32_t h, int i) {
-    return (h * direction_mult(i)) >> 16;
-}
-// The draws of direction i for two nodes in one word: direction_bits(h_lo, i)
-// in the low and direction_bits(h_hi, i) in the high 16 bits (the upper
-// halves of the two products, gathered by one byte permutation).
-__device__ __forceinline__ uint32_t direction_bits2(uint32_t h_lo, uint32_t h_hi, int i) {
-    return __byte_perm(h_lo * direction_mult(i), h_hi * direction_mult(i), 0x7632);
+__device__ __forceinline__ uint32_t pair_bits(uint32_t h, int i) {
+    const uint32_t r = h * direction_mult(i);
+    return r ^ (r >> 16);
 }
 
 // 16-byte vector of V stored elements.

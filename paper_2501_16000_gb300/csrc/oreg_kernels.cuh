@@ -69,8 +69,9 @@ __device__ __forceinline__ void zero_padding(typename Storage<S>::C f[9][Storage
 // Encodes the post-collision values to the storage format: round to nearest,
 // or (half formats, sr) stochastically with counter-based bits per node,
 // time step and direction.
-// Half formats encode node pairs (j, j+1) with one packed conversion; the
-// stochastic draw of node x, direction i is direction_bits(node_seed(x, y, t), i).
+// Half formats encode node pairs (x, x+1), x even, with one packed
+// conversion; the stochastic draws of a pair and direction i are
+// pair_bits(node_seed(x / 2, y, t), i).
 template <int S>
 __device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Storage<S>::V],
                                            typename Storage<S>::T e[9][Storage<S>::V], int xb,
@@ -82,10 +83,10 @@ __device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Sto
         if (sr) {
 #pragma unroll
             for (int j = 0; j < ST::V; j += 2) {
-                const uint32_t h0 = node_seed(xb + j, y, t), h1 = node_seed(xb + j + 1, y, t);
+                const uint32_t h = node_seed((xb + j) >> 1, y, t);
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
-                    w[i][j / 2] = ST::enc2_stochastic(f[i][j], f[i][j + 1], direction_bits2(h0, h1, i));
+                    w[i][j / 2] = ST::enc2_stochastic(f[i][j], f[i][j + 1], pair_bits(h, i));
             }
         } else {
 #pragma unroll
