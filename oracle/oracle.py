@@ -8,7 +8,7 @@ into ``oracle/_build/`` on first use and exposes numpy-level calls.
 Each call restates one passage of arXiv 2501.16000:
   feq          Eq. 11 (guided) / Eq. 15 (polynomial, -u^2/(2 theta0) restored)
   foreg        Eq. 6
-  collide      Eq. 7 (OReg) or Eq. 1 (BGK), one node
+  collide      Eq. 7 (OReg) or Eq. 1 (BGK), one node (fixed or local temperature)
   stream       streaming of Eqs. 1/7 (x -> x + c_i, periodic)
   step / run   collide (or bounce back at wall nodes) + stream at every node
   first_order  Eq. 5, one node; init_first_order: S_0 = f^eq + f^(1)
@@ -40,7 +40,7 @@ class OraParams(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("theta", ctypes.c_double),
                 ("eq", ctypes.c_int32), ("coll", ctypes.c_int32),
-                ("walls", ctypes.c_int32)]
+                ("walls", ctypes.c_int32), ("theta_local", ctypes.c_int32)]
 
 
 def build(force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:
@@ -79,6 +79,8 @@ def load(path: str) -> ctypes.CDLL:
                             ctypes.c_double, ctypes.c_double, d]
     L.ora_collide_node.argtypes = [P, d, d]
     L.ora_bounce_back_node.argtypes = [d, d]
+    L.ora_node_theta.argtypes = [d, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.ora_node_theta.restype = ctypes.c_double
     L.ora_stream.argtypes = [ctypes.c_int32, ctypes.c_int32, d, d]
     L.ora_step.argtypes = [P, d, d]
     L.ora_run.argtypes = [P, d, d, ctypes.c_int64]
@@ -139,10 +141,12 @@ def get_threads() -> int:
     return int(lib().ora_get_threads())
 
 
-def params(nx, ny, tau, theta=1.0 / 3.0, eq=GUIDED, coll=OREG, walls=False) -> OraParams:
-    """walls: columns x = 0 and nx - 1 are full-way bounce-back walls."""
+def params(nx, ny, tau, theta=1.0 / 3.0, eq=GUIDED, coll=OREG, walls=False,
+           theta_local=False) -> OraParams:
+    """walls: columns x = 0 and nx - 1 are full-way bounce-back walls.
+    theta_local: the guided equilibrium and Eq. 6 use each node's temperature."""
     return OraParams(int(nx), int(ny), float(tau), float(theta), int(eq), int(coll),
-                     1 if walls else 0)
+                     1 if walls else 0, 1 if theta_local else 0)
 
 
 def feq(eq: int, theta: float, rho: float, ux: float, uy: float) -> np.ndarray:
@@ -170,10 +174,10 @@ def foreg(f, eq: int, theta: float) -> np.ndarray:
 
 
 def collide(f, tau: float, theta: float = 1.0 / 3.0, eq: int = GUIDED,
-            coll: int = OREG) -> np.ndarray:
+            coll: int = OREG, theta_local: bool = False) -> np.ndarray:
     f = _f64(f)
     out = np.zeros(9)
-    p = params(1, 1, tau, theta, eq, coll)
+    p = params(1, 1, tau, theta, eq, coll, theta_local=theta_local)
     lib().ora_collide_node(ctypes.byref(p), _p(f), _p(out))
     return out
 

@@ -56,6 +56,10 @@ typedef struct {
     int32_t coll;     /* 0 = OReg (Eq. 7), 1 = BGK (Eq. 1) */
     int32_t walls;    /* 1: columns x = 0 and x = nx - 1 are full-way
                          bounce-back walls (Sec. IV shock tube); 0: periodic */
+    int32_t theta_local; /* guided only.  0: theta is the fixed lattice
+                            temperature (isothermal, Sec. II); 1: each node's
+                            equilibrium and Eq. 6 use the node's own
+                            temperature (<f,c^2> - rho u^2) / (D rho) */
 } ora_params;
 
 /* Reference temperature of the polynomial equilibrium (Eq. 15). */
@@ -179,15 +183,27 @@ void ora_foreg(const double *f, const double *feq, double rho, double ux, double
     }
 }
 
+/* Temperature of one node's populations: E = <f, c^2/2> = (D p + rho u^2)/2
+ * with p = rho theta (Eq. 2a and the definitions after Eq. 2), solved for
+ * theta = (<f, c^2> - rho u^2) / (D rho). */
+double ora_node_theta(const double *f, double rho, double ux, double uy) {
+    double c2f = 0.0;
+    for (int i = 0; i < ORA_Q; ++i)
+        c2f += (double)(ORA_C[i][0] * ORA_C[i][0] + ORA_C[i][1] * ORA_C[i][1]) * f[i];
+    return (c2f - rho * (ux * ux + uy * uy)) / ((double)ORA_D * rho);
+}
+
 /* One node's collision.  OReg (Eq. 7): post_i = f_i^eq + (1 - 1/tau) f_i^OReg.
- * BGK (Eq. 1): post_i = f_i - (1/tau) (f_i - f_i^eq). */
+ * BGK (Eq. 1): post_i = f_i - (1/tau) (f_i - f_i^eq).  With theta_local the
+ * guided equilibrium and Eq. 6 take the node's own temperature. */
 void ora_collide_node(const ora_params *p, const double *f, double *post) {
     double rho, ux, uy, feq[ORA_Q];
     ora_node_moments(f, &rho, &ux, &uy);
-    ora_feq(p->eq, p->theta, rho, ux, uy, feq);
+    const double theta = p->theta_local ? ora_node_theta(f, rho, ux, uy) : p->theta;
+    ora_feq(p->eq, theta, rho, ux, uy, feq);
     if (p->coll == 0) {
         double foreg[ORA_Q];
-        ora_foreg(f, feq, rho, ux, uy, ora_theta_eff(p->eq, p->theta), foreg);
+        ora_foreg(f, feq, rho, ux, uy, ora_theta_eff(p->eq, theta), foreg);
         for (int i = 0; i < ORA_Q; ++i)
             post[i] = feq[i] + (1.0 - 1.0 / p->tau) * foreg[i];
     } else {

@@ -28,6 +28,10 @@ invariants.  None is produced by re-running the oracle's own formula:
   from them decays at the viscous rate from the first step.
 * Fig. 2a: an axis-aligned shear wave on a mean flow along its wave vector
   decays at the imposed viscosity and is advected at U.k.
+* Local temperature: BGK conserves <f, c^2> at every node (Eq. 2a energy of
+  the guided equilibrium), OReg changes it by (1 - 1/tau) x the trace of
+  Eq. 12b; sound travels at sqrt(theta) (isothermal) and at sqrt(2 theta)
+  (gamma = 2 for D = 2) with the local temperature.
 * Full-way bounce-back walls: exact mass, the rest state as a fixed point,
   the slowest viscous mode between no-slip walls placed halfway between wall
   and fluid columns, and the Sec. IV shock tube between walls against the
@@ -509,6 +513,78 @@ def check_shock_tube():
 
 
 # ---------------------------------------------------------------------------
+# local temperature (the guided equilibrium taking each node's own theta)
+# ---------------------------------------------------------------------------
+
+def check_local_theta_energy():
+    """With the node's own temperature theta = (<f,c^2> - rho u^2)/(2 rho), the
+    guided equilibrium carries the node's energy (Eq. 2a: <f^eq, c^2/2> = E),
+    so BGK conserves <f, c^2> at every node, and OReg changes it by exactly
+    (1 - 1/tau) times the trace of Eq. 12b's stress of f^OReg,
+    S_xx [(theta - u_x^2)(1 - theta - u_x^2) - (theta - u_y^2)(1 - theta - u_y^2)]
+    / (2 theta^2).  A uniform state at any temperature is a fixed point."""
+    c = _c()
+    c2 = (c ** 2).sum(1)
+    rng = np.random.default_rng(RNG_SEED + 31)
+    for _ in range(40):
+        rho = rng.uniform(0.7, 1.4)
+        ux, uy = rng.uniform(-0.2, 0.2, 2)
+        th = rng.uniform(0.25, 0.45)
+        sxx, sxy = rng.uniform(-0.02, 0.02, 2)
+        f = _with_stress(O.GUIDED, th, rho, ux, uy, sxx, sxy, [0.0, 0.0, 0.0, 0.0])
+        # a zero non-equilibrium trace keeps the node's temperature at th
+        tau = rng.uniform(0.52, 1.5)
+        post_b = O.collide(f, tau, 0.3, O.GUIDED, O.BGK, theta_local=True)
+        _close(c2 @ post_b, c2 @ f, 1e-15, "BGK energy with the local temperature")
+        post_o = O.collide(f, tau, 0.3, O.GUIDED, O.OREG, theta_local=True)
+        tr = sxx * ((th - ux ** 2) * (1 - th - ux ** 2) - (th - uy ** 2) * (1 - th - uy ** 2)) / (
+            2 * th ** 2)
+        _close(c2 @ post_o - c2 @ f, (1 - 1 / tau) * tr, 1e-15,
+               "OReg energy change with the local temperature (Eq. 12b trace)")
+        _close(post_o.sum(), f.sum(), 1e-15, "mass with the local temperature")
+    for th in (0.2, 0.3, 0.45):
+        f = O.feq(O.GUIDED, th, 1.2, 0.03, -0.05)
+        for coll in (O.OREG, O.BGK):
+            _close(O.collide(f, 0.7, 1 / 3, O.GUIDED, coll, theta_local=True), f, 1e-15,
+                   "uniform state at its own temperature")
+
+
+def _density_wave_speed(coll, theta_local, isentropic, L=64, tau=0.6, th0=1 / 3, steps=400):
+    """Sound speed from the zero crossings of the density mode of a standing
+    wave rho = 1 + eps cos(k x), u = 0 (temperature perturbed adiabatically
+    if isentropic)."""
+    x = np.arange(L)
+    cs = np.cos(2 * np.pi * x / L)
+    eps = 1e-4
+    rho = 1 + eps * cs
+    th = th0 * (1 + eps * cs) if isentropic else np.full(L, th0)
+    f = np.zeros((9, 1, L))
+    for i in range(L):
+        f[:, 0, i] = O.feq(O.GUIDED, th[i], rho[i], 0.0, 0.0)
+    p = O.params(L, 1, tau, th0, O.GUIDED, coll, theta_local=theta_local)
+    amp = []
+    for _ in range(steps + 1):
+        amp.append(np.sum((O.fields(f)[0][0] - 1) * cs))
+        f = O.step(f, p)
+    amp = np.array(amp)
+    zc = [t + amp[t] / (amp[t] - amp[t + 1]) for t in range(steps) if amp[t] * amp[t + 1] < 0]
+    return (2 * np.pi / (2 * np.mean(np.diff(zc)))) / (2 * np.pi / L)
+
+
+def check_local_theta_sound_speed():
+    """Sound speed c_s = sqrt(gamma theta): gamma = 1 in the isothermal scheme
+    (fixed theta) and gamma = (D + 2)/D = 2 for the two-dimensional monatomic
+    gas once each node's equilibrium carries its own temperature (adiabatic
+    sound; the guided equilibrium's heat-flux defect, Sec. III, vanishes to
+    first order in u at theta = 1/3)."""
+    for coll in (O.OREG, O.BGK):
+        c_iso = _density_wave_speed(coll, False, False)
+        assert abs(c_iso / math.sqrt(1 / 3) - 1) < 1e-3, (coll, c_iso)
+        c_ad = _density_wave_speed(coll, True, True)
+        assert abs(c_ad / math.sqrt(2 / 3) - 1) < 1e-3, (coll, c_ad)
+
+
+# ---------------------------------------------------------------------------
 # full-way bounce-back wall columns (Sec. IV shock tube)
 # ---------------------------------------------------------------------------
 
@@ -599,4 +675,5 @@ FAST_CHECKS = [
 ]
 LATTICE_CHECKS = [check_shear_wave_decay, check_shear_wave_decay_off_reference_temperature,
                   check_first_order_start, check_mean_flow_axis_wave, check_shock_tube,
-                  check_walls_conservation, check_walls_shear_decay, check_walls_shock_tube]
+                  check_walls_conservation, check_walls_shear_decay, check_walls_shock_tube,
+                  check_local_theta_energy, check_local_theta_sound_speed]

@@ -69,6 +69,14 @@ MUTATIONS = [
     ("wall column off by one", "if (p->walls && (x == 0 || x == nx - 1))",
      "if (p->walls && (x == 1 || x == nx - 1))"),
     ("walls ignored", "if (p->walls && (x == 0 || x == nx - 1))", "if (0)"),
+    ("local theta keeps rho u^2", "return (c2f - rho * (ux * ux + uy * uy)) / ((double)ORA_D * rho);",
+     "return c2f / ((double)ORA_D * rho);"),
+    ("local theta not divided by D", "return (c2f - rho * (ux * ux + uy * uy)) / ((double)ORA_D * rho);",
+     "return (c2f - rho * (ux * ux + uy * uy)) / rho;"),
+    ("local theta missing in Eq. 6", "ora_foreg(f, feq, rho, ux, uy, ora_theta_eff(p->eq, theta), foreg);",
+     "ora_foreg(f, feq, rho, ux, uy, ora_theta_eff(p->eq, p->theta), foreg);"),
+    ("local theta ignored", "const double theta = p->theta_local ? ora_node_theta(f, rho, ux, uy) : p->theta;",
+     "const double theta = p->theta;"),
     ("streaming-only path wraps the wrong axis", "ora_wrap(x + ORA_C[i][0], nx);\n                dst[i * N + yd * nx + xd] = post[i * N",
      "ora_wrap(x + ORA_C[i][1], nx);\n                dst[i * N + yd * nx + xd] = post[i * N"),
 ]
