@@ -80,6 +80,16 @@ typedef enum { OLB_LAYOUT_AB = 0, OLB_LAYOUT_AA = 1 } olb_layout;
  * total mass over all nodes stays exactly conserved.  Needs nx >= 3. */
 typedef enum { OLB_BOUNDARY_PERIODIC = 0, OLB_BOUNDARY_WALLS_X = 1 } olb_boundary;
 
+/* FIXED: theta is the lattice's fixed temperature in the guided equilibrium
+ * (Eq. 11) and in Eq. 6 (isothermal flow, Sec. II; the paper's runs).
+ * LOCAL: every node uses its own temperature
+ * theta = (<f,c^2> - rho u^2) / (2 rho) (Eq. 2a: E = (D p + rho u^2)/2,
+ * p = rho theta); the guided equilibrium then carries the node's energy, so
+ * BGK conserves <f,c^2> and sound travels at sqrt(2 theta) (gamma = 2 in two
+ * dimensions); p->theta is the reference temperature of the storage shift
+ * and of the initialisers.  Guided equilibrium only. */
+typedef enum { OLB_THETA_FIXED = 0, OLB_THETA_LOCAL = 1 } olb_theta_mode;
+
 typedef struct {
     int32_t nx, ny;        /* lattice size, >= 1 each */
     double tau;            /* relaxation time, > 0.5 */
@@ -98,6 +108,7 @@ typedef struct {
     void *cuda_stream;     /* cudaStream_t for all work of this lattice;
                               NULL: the library creates and owns one */
     int32_t boundary;      /* olb_boundary (0: periodic) */
+    int32_t theta_mode;    /* olb_theta_mode (0: fixed) */
 } olb_params;
 
 /* Tuning and precision options of a lattice (olb_set_option). */
@@ -123,8 +134,8 @@ typedef enum {
     OLB_OPT_STOCHASTIC_ROUNDING = 3
 } olb_option;
 
-/* Version of this ABI (bumped on incompatible change); 2 since
- * olb_params.boundary. */
+/* Version of this ABI (bumped on incompatible change); 3 since
+ * olb_params.theta_mode. */
 int32_t olb_abi_version(void);
 
 /* Bytes of device memory the populations of a lattice with these

@@ -56,7 +56,7 @@ class BatchEngine:
         initialised (not yet added)."""
         lat = Lattice(case.nx, case.ny, case.tau, case.theta, case.eq, case.coll, self.storage,
                       self.layout, torch_memory=True, stream=self.stream,
-                      boundary=case.boundary, **kw)
+                      boundary=case.boundary, theta_mode=case.theta_mode, **kw)
         lat.init_case(case)
         return lat
 

@@ -43,11 +43,13 @@ class olb_params(ctypes.Structure):
                 ("eq", ctypes.c_int32), ("coll", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("device_buffer", ctypes.c_void_p), ("buffer_bytes", ctypes.c_size_t),
-                ("cuda_stream", ctypes.c_void_p), ("boundary", ctypes.c_int32)]
+                ("cuda_stream", ctypes.c_void_p), ("boundary", ctypes.c_int32),
+                ("theta_mode", ctypes.c_int32)]
 
 
-ABI_VERSION = 2
+ABI_VERSION = 3
 BOUNDARY = {"periodic": 0, "walls_x": 1}
+THETA_MODE = {"fixed": 0, "local": 1}
 
 
 class olb_batch_params(ctypes.Structure):

@@ -91,6 +91,10 @@ olb_status validate(const olb_params *p) {
         return fail(OLB_ERR_INVALID, "unknown boundary %d", p->boundary);
     if (p->boundary == OLB_BOUNDARY_WALLS_X && p->nx < 3)
         return fail(OLB_ERR_INVALID, "wall columns need nx >= 3 (got %d)", p->nx);
+    if (p->theta_mode != OLB_THETA_FIXED && p->theta_mode != OLB_THETA_LOCAL)
+        return fail(OLB_ERR_INVALID, "unknown theta mode %d", p->theta_mode);
+    if (p->theta_mode == OLB_THETA_LOCAL && p->eq != OLB_EQ_GUIDED)
+        return fail(OLB_ERR_INVALID, "the local temperature needs the guided equilibrium");
     return OLB_OK;
 }
 
@@ -293,7 +297,7 @@ olb_status mode_tables(olb_lattice *L, int m, int n) {
 
 extern "C" {
 
-int32_t olb_abi_version(void) { return 2; }
+int32_t olb_abi_version(void) { return 3; }
 
 size_t olb_required_bytes(const olb_params *p) {
     if (validate(p) != OLB_OK) return 0;
@@ -489,7 +493,7 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     a.plane = L->plane;
     a.lw = segment_log2(L->p.nx, L->V);
     a.segs = (L->p.nx + (L->V << a.lw) - 1) / (L->V << a.lw);
-    a.eq = L->p.eq;
+    a.eq = kernel_eq(&L->p);
     a.coll = L->p.coll;
     a.layout = L->p.layout;
     a.comp = L->comp;

@@ -47,8 +47,8 @@ olb_status bcuda(cudaError_t e, const char *what) {
      : (storage) == OLB_F16_SHIFTED ? fn##_f16(__VA_ARGS__)             \
                                     : fn##_bf16(__VA_ARGS__))
 
-// item groups: (walls, equilibrium, collision, parity class)
-constexpr int NGROUPS = 16;
+// item groups: (walls, equilibrium kind, collision, parity class)
+constexpr int NGROUPS = 24;
 
 struct Member {
     olb_lattice *lat;
@@ -90,7 +90,7 @@ struct olb_batch {
     // device tables
     char *d_descs;
     int4 *d_items;
-    int *d_groups;          // item offsets of the 16 (walls, eq, coll, parity class) groups
+    int *d_groups;          // item offsets of the 24 (walls, eq kind, coll, parity class) groups
     long long *d_g;
     // host mirrors
     std::vector<Member> members;
@@ -100,6 +100,7 @@ struct olb_batch {
     long long G;            // global step counter at the start of the next round
     bool captured;
     bool graph_walls;       // the captured graph launches the wall-column kernels
+    bool graph_local;       // ... and the local-temperature kernels
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
@@ -117,7 +118,8 @@ olb_status upload(olb_batch *b) {
         else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf);
         const int cls = (int)((m.t_base - m.g_base) & 1);
         const int walls = L->p.boundary == OLB_BOUNDARY_WALLS_X;
-        const int grp = ((walls * 2 + L->p.eq) * 2 + L->p.coll) * 2 + cls;
+        const int eqk = kernel_eq(&L->p);
+        const int grp = ((walls * 3 + eqk) * 2 + L->p.coll) * 2 + cls;
         const int lw = segment_log2(L->p.nx, L->V);
         const int segs = (L->p.nx + (L->V << lw) - 1) / (L->V << lw);
         const int rows = 32 >> lw;  // rows per warp item
@@ -162,8 +164,11 @@ olb_status capture(olb_batch *b) {
     a.block = b->block;
     a.stream = b->stream;
     a.walls = 0;
-    for (const Member &m : b->members)
+    a.local_theta = 0;
+    for (const Member &m : b->members) {
         if (m.lat->p.boundary == OLB_BOUNDARY_WALLS_X) a.walls = 1;
+        if (kernel_eq(&m.lat->p) == EQ_GUIDED_LOCAL) a.local_theta = 1;
+    }
     B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
            "beginning graph capture");
     cudaError_t e = cudaSuccess;
@@ -186,6 +191,7 @@ olb_status capture(olb_batch *b) {
     B_CUDA(cudaGraphInstantiate(&b->exec, g, 0), "instantiating batch graph");
     b->captured = true;
     b->graph_walls = a.walls != 0;
+    b->graph_local = a.local_theta != 0;
     return OLB_OK;
 }
 
@@ -279,8 +285,10 @@ olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps) {
         return st;
     }
     lat->batch = b;
-    if (b->captured && !b->graph_walls && lat->p.boundary == OLB_BOUNDARY_WALLS_X) {
-        // the graph lacks the wall-column kernels: capture again on the next run
+    const bool needs_walls = lat->p.boundary == OLB_BOUNDARY_WALLS_X && !b->graph_walls;
+    const bool needs_local = kernel_eq(&lat->p) == EQ_GUIDED_LOCAL && !b->graph_local;
+    if (b->captured && (needs_walls || needs_local)) {
+        // the graph lacks this lattice's kernels: capture again on the next run
         cudaGraphExecDestroy(b->exec);
         cudaGraphDestroy(b->graph);
         b->exec = nullptr;

@@ -34,15 +34,17 @@ template <typename C> struct BatchDesc {
     CollConst<C> k;
 };
 
-// Work items are grouped on the host by (walls, equilibrium, collision,
-// parity class): group = ((walls * 2 + eq) * 2 + coll) * 2 + c, with
+// Work items are grouped on the host by (walls, equilibrium kind, collision,
+// parity class): group = ((walls * 3 + eq) * 2 + coll) * 2 + c, with eq the
+// kernel's equilibrium kind (guided, polynomial, guided at the local
+// temperature) and
 // c = (t_base - g_base) & 1 the lattice's fixed offset between its own time
 // and the global step, so that at global step g every lattice of class c has
 // time parity (g + c) & 1.  Each kernel below handles one (walls, eq, coll)
 // and, for the in-place layout, one parity: one item body per kernel keeps
-// register use at the single-lattice kernels' level.  groups[0..16] are the
-// item offsets of the 16 groups; the bounce-back (walls) kernels are only
-// launched by batches that hold a lattice with wall columns.
+// register use at the single-lattice kernels' level.  groups[0..24] are the
+// item offsets of the 24 groups; the bounce-back (walls) and local-temperature
+// kernels are only launched by batches that hold such a lattice.
 enum { BATCH_AB = 0, BATCH_AA_EVEN = 1, BATCH_AA_ODD = 2 };
 
 // 256 threads x 2 blocks per SM caps registers at 128 per thread: the
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(256, 2)
                  const long long *__restrict__ g_round, int k) {
     using T = typename Storage<S>::T;
     const long long g = *g_round + k;
-    constexpr int combo = ((WALLS ? 1 : 0) * 2 + EQ) * 2 + COLL;
+    constexpr int combo = ((WALLS ? 1 : 0) * 3 + EQ) * 2 + COLL;
     int lo, hi;
     if constexpr (KIND == BATCH_AB) {
         lo = groups[combo * 2];
@@ -103,6 +105,12 @@ template <int S> struct BatchLaunchT {
             descs, a.items, a.groups, a.g, a.k);
         k_batch_step<S, KIND, EQ_POLY2, COLL_BGK, WALLS><<<a.grid, a.block, 0, a.stream>>>(
             descs, a.items, a.groups, a.g, a.k);
+        if (a.local_theta) {
+            k_batch_step<S, KIND, EQ_GUIDED_LOCAL, COLL_OREG, WALLS><<<a.grid, a.block, 0, a.stream>>>(
+                descs, a.items, a.groups, a.g, a.k);
+            k_batch_step<S, KIND, EQ_GUIDED_LOCAL, COLL_BGK, WALLS><<<a.grid, a.block, 0, a.stream>>>(
+                descs, a.items, a.groups, a.g, a.k);
+        }
     }
     template <int KIND>
     static cudaError_t launch_kind(const BatchLaunch &a) {

@@ -41,7 +41,9 @@ __host__ __device__ constexpr int dcls(int i) {
 static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp");
 static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp");
 
-enum { EQ_GUIDED = 0, EQ_POLY2 = 1 };
+// Equilibrium kinds of the kernels: guided at the lattice's fixed theta,
+// polynomial, and guided at each node's own temperature (local theta).
+enum { EQ_GUIDED = 0, EQ_POLY2 = 1, EQ_GUIDED_LOCAL = 2 };
 enum { COLL_OREG = 0, COLL_BGK = 1 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
@@ -320,7 +322,8 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
     // sums between the conserved moments and the stress and fold the OReg
     // prefactor into the stress; float and double keep the plain order.
     constexpr bool PACKED = std::is_same<C, F2>::value;
-    C drho, jx, jy, dxy, pxy;
+    constexpr bool LOCAL = EQ == EQ_GUIDED_LOCAL;
+    C drho, jx, jy, dxy, pxy, tg = C(0);
     if constexpr (PACKED && !COMP) {
         const C s13 = g[1] + g[3], s24 = g[2] + g[4], s57 = g[5] + g[7], s68 = g[6] + g[8];
         const C d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d68 = g[6] - g[8];
@@ -329,15 +332,30 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         jy = (d24 + d57) + d68;
         dxy = s13 - s24;
         pxy = s57 - s68;
+        if constexpr (LOCAL) tg = (s13 + s24) + C(2) * (s57 + s68);
     } else {
         conserved<C, COMP>(g, k, drho, jx, jy);
         dxy = (g[1] + g[3]) - (g[2] + g[4]);
         pxy = (g[5] + g[7]) - (g[6] + g[8]);
+        if constexpr (LOCAL) tg = ((g[1] + g[3]) + (g[2] + g[4])) + C(2) * ((g[5] + g[7]) + (g[6] + g[8]));
     }
     const C rho = k.rho0 + drho;
     const C inv_rho = C(1) / rho;
     const C ux = jx * inv_rho, uy = jy * inv_rho;
     const C ux2 = ux * ux, uy2 = uy * uy;
+    // Local temperature (EQ_GUIDED_LOCAL): 2 rho theta = <f,c^2> - rho u^2
+    // (Eq. 2a energy), written as theta = theta_ref + dth with
+    // 2 rho dth = sum c^2 g - sum c^2 corr - 2 theta_ref drho - rho u^2, all
+    // small deviations (the shifts' own sum c^2 s = 2 theta_ref rho0 - sum
+    // c^2 corr cancels exactly).  Psi_0 = 1 - theta - u^2 and
+    // Psi_+- = (theta +- u + u^2)/2 then deviate from their rest values at
+    // theta_ref by dth as well as by u.
+    C dth = C(0);
+    if constexpr (LOCAL) {
+        const C c2corr = C(4) * k.corr[1] + C(8) * k.corr[2];
+        dth = C(0.5) * inv_rho *
+              (((tg - c2corr) - C(2) * k.theta * drho) - rho * (ux2 + uy2));
+    }
 
     // The equilibrium constants enter in hi + lo form.  Rounded to C alone
     // they would break sum_b Psi_b(0) = 1 and sum_i W_i c_i c_i = theta by a
@@ -345,11 +363,13 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
     // node at every step; in FP32 that bias, not random rounding, dominates
     // the drift from the FP64 result over thousands of steps.
     C geq[9];
-    if constexpr (EQ == EQ_GUIDED) {
-        // dPsi_+- = u^2/2 +- u/2, dPsi_0 = -u^2 (u/2 and u^2/2 are exact halvings)
-        const C qx = C(0.5) * ux, hx = C(0.5) * ux2, qy = C(0.5) * uy, hy = C(0.5) * uy2;
-        const C dpx[3] = {-ux2, hx + qx, hx - qx};
-        const C dpy[3] = {-uy2, hy + qy, hy - qy};
+    if constexpr (EQ == EQ_GUIDED || LOCAL) {
+        // dPsi_+- = u^2/2 +- u/2, dPsi_0 = -u^2 (u/2 and u^2/2 are exact halvings);
+        // with the local temperature u^2 -> u^2 + dth
+        const C ex2 = LOCAL ? ux2 + dth : ux2, ey2 = LOCAL ? uy2 + dth : uy2;
+        const C qx = C(0.5) * ux, hx = C(0.5) * ex2, qy = C(0.5) * uy, hy = C(0.5) * ey2;
+        const C dpx[3] = {-ex2, hx + qx, hx - qx};
+        const C dpy[3] = {-ey2, hy + qy, hy - qy};
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
@@ -380,7 +400,13 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
     } else {
         const C sxx = C(0.5) * (dxy - rho * (ux2 - uy2));
         const C sxy = pxy - rho * ux * uy;
-        const C a = k.lam * k.inv_2th2 * inv_rho;
+        C a;
+        if constexpr (LOCAL) {
+            const C th = k.theta + dth;
+            a = k.lam / (C(2) * th * th * rho);
+        } else {
+            a = k.lam * k.inv_2th2 * inv_rho;
+        }
         const C X[3] = {-ux, C(1) - ux, C(-1) - ux};
         const C Y[3] = {-uy, C(1) - uy, C(-1) - uy};
         if constexpr (PACKED) {

@@ -423,6 +423,9 @@ template <int S> struct StepLaunch {
         if (a.eq == EQ_GUIDED) {
             if (a.coll == COLL_OREG) step_eq<EQ_GUIDED, COLL_OREG, COMP, WALLS>(a, grid, block);
             else step_eq<EQ_GUIDED, COLL_BGK, COMP, WALLS>(a, grid, block);
+        } else if (a.eq == EQ_GUIDED_LOCAL) {
+            if (a.coll == COLL_OREG) step_eq<EQ_GUIDED_LOCAL, COLL_OREG, COMP, WALLS>(a, grid, block);
+            else step_eq<EQ_GUIDED_LOCAL, COLL_BGK, COMP, WALLS>(a, grid, block);
         } else {
             if (a.coll == COLL_OREG) step_eq<EQ_POLY2, COLL_OREG, COMP, WALLS>(a, grid, block);
             else step_eq<EQ_POLY2, COLL_BGK, COMP, WALLS>(a, grid, block);

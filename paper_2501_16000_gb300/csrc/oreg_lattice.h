@@ -44,4 +44,10 @@ struct olb_lattice {
 namespace oreg {
 // Records the message of a failed call for olb_last_error() (oreg_api.cu).
 void set_last_error_message(const char *msg);
+
+// Equilibrium kind of the stream-collide kernels for a lattice.
+inline int kernel_eq(const olb_params *p) {
+    if (p->eq == OLB_EQ_GUIDED && p->theta_mode == OLB_THETA_LOCAL) return EQ_GUIDED_LOCAL;
+    return p->eq == OLB_EQ_GUIDED ? EQ_GUIDED : EQ_POLY2;
+}
 }  // namespace oreg

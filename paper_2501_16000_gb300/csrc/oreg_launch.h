@@ -28,7 +28,8 @@ struct StepArgs {
     size_t plane;
     int segs;          // row segments of W*V nodes per row
     int lw;            // log2 of W, the lanes per row segment (W <= 32)
-    int eq, coll, layout, parity;
+    int eq, coll, layout, parity;  // eq: kernel equilibrium kind (EQ_GUIDED_LOCAL for
+                                   // the guided equilibrium at the local temperature)
     int comp;          // compensated conserved-moment sums (FP32 only)
     int sr;            // stochastic rounding (half formats only)
     int walls;         // full-way bounce-back wall columns x = 0 and x = nx - 1
@@ -96,11 +97,12 @@ OREG_DECLARE_LAUNCHERS(bf16)
 struct BatchLaunch {
     const void *descs;        // BatchDesc<C>[]
     const int4 *items;        // work items (descriptor, first row, segment), grouped
-    const int *groups;        // device: item offsets of the 16 groups (17 entries)
+    const int *groups;        // device: item offsets of the 24 groups (25 entries)
     const long long *g;       // device: global step counter of this round
     int k;                    // step within the round
     int layout;
     int walls;                // also launch the bounce-back (wall column) kernels
+    int local_theta;          // also launch the local-temperature kernels
     int grid, block;
     cudaStream_t stream;
 };

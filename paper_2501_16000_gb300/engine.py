@@ -30,10 +30,11 @@ def _dptr(a: np.ndarray):
 
 def make_params(nx, ny, tau, theta=1.0 / 3.0, eq="guided", coll="oreg", storage="f32",
                 layout="ab", rho0=1.0, device_buffer=0, buffer_bytes=0, stream=0,
-                boundary="periodic"):
+                boundary="periodic", theta_mode="fixed"):
     return B.olb_params(int(nx), int(ny), float(tau), float(theta), float(rho0), EQ[eq],
                         COLL[coll], STORAGE[storage], LAYOUT[layout], device_buffer or None,
-                        int(buffer_bytes), stream or None, B.BOUNDARY[boundary])
+                        int(buffer_bytes), stream or None, B.BOUNDARY[boundary],
+                        B.THETA_MODE[theta_mode])
 
 
 def required_bytes(**kw) -> int:
@@ -50,15 +51,15 @@ class Lattice:
 
     def __init__(self, nx, ny, tau, theta=1.0 / 3.0, eq="guided", coll="oreg",
                  storage="f32", layout="ab", rho0=1.0, torch_memory=None, stream=None,
-                 boundary="periodic"):
+                 boundary="periodic", theta_mode="fixed"):
         self.nx, self.ny, self.tau, self.theta = int(nx), int(ny), float(tau), float(theta)
         self.eq, self.coll, self.storage, self.layout = eq, coll, storage, layout
-        self.boundary = boundary
+        self.boundary, self.theta_mode = boundary, theta_mode
         self._buf = None
         self._handle = None
         self.stream = None  # torch stream the lattice runs on (torch memory only)
         kw = dict(nx=nx, ny=ny, tau=tau, theta=theta, eq=eq, coll=coll, storage=storage,
-                  layout=layout, rho0=rho0, boundary=boundary)
+                  layout=layout, rho0=rho0, boundary=boundary, theta_mode=theta_mode)
         dev_ptr, nbytes, sptr = 0, 0, 0
         if torch_memory is None:
             try:

@@ -152,7 +152,7 @@ def serve_serial(trace, storage="f32", layout="ab", time_scale: float = 1.0, kee
         c = req.lattice
         start = now()
         with Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, storage, layout,
-                     boundary=c.boundary) as lat:
+                     boundary=c.boundary, theta_mode=c.theta_mode) as lat:
             lat.init_case(c)
             lat.step(c.steps)
             fields = lat.moments() if keep_fields else None

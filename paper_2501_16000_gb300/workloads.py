@@ -132,6 +132,7 @@ class LatticeCase:
     uy_mean: float = 0.0
     first_order: bool = False   # start from f^eq + f^(1) of Eq. 5 (shear only)
     boundary: str = "periodic"  # or "walls_x": bounce-back wall columns x = 0, nx - 1
+    theta_mode: str = "fixed"   # or "local": guided equilibrium at each node's temperature
 
     @property
     def nodes(self) -> int:
