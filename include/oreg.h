@@ -257,11 +257,12 @@ typedef struct {
     int32_t layout;            /* olb_layout of every member */
     int32_t max_lattices;      /* descriptor capacity */
     int64_t max_items;         /* work-item capacity: sum over members of
-                                  ceil(ny / (32 / W)) * ceil(nx / (W * V)),
+                                  ceil(ceil(ny / (32 / W)) / 4) * ceil(nx / (W * V)),
                                   V = 16 / element size, W the smallest power
-                                  of two <= 32 with W * V >= nx */
+                                  of two <= 32 with W * V >= nx (an item is up
+                                  to 4 groups of 32 / W rows of one segment) */
     int32_t steps_per_launch;  /* K: time steps per graph replay (1..10000) */
-    int32_t warps_per_block;   /* 1, 2, 4 or 8 */
+    int32_t warps_per_block;   /* 1, 2 or 4 */
     int32_t blocks_per_sm;     /* persistent grid = blocks_per_sm x SMs;
                                   0 = the kernel's occupancy limit */
     void *cuda_stream;         /* stream of the batch and of every member;

@@ -20,17 +20,21 @@ from .engine import LAYOUT, STORAGE, Lattice
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
+ITEM_ROW_GROUPS = 4
+
+
 def work_items(nx: int, ny: int, storage: str) -> int:
-    """Warp work items of one lattice: a warp covers 32/W rows of W-lane row
-    segments, W the smallest power of two <= 32 whose W 16-byte vectors span
-    the row."""
+    """Warp work items of one lattice: a warp pass covers a row group of 32/W
+    rows of W-lane row segments, W the smallest power of two <= 32 whose W
+    16-byte vectors span the row; an item is up to ITEM_ROW_GROUPS row groups
+    of one segment."""
     v = 16 // {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[storage]
     vecs = math.ceil(nx / v)
     lw = 0
     while lw < 5 and (1 << lw) < vecs:
         lw += 1
     w = 1 << lw
-    return math.ceil(ny / (32 // w)) * math.ceil(nx / (w * v))
+    return math.ceil(math.ceil(ny / (32 // w)) / ITEM_ROW_GROUPS) * math.ceil(nx / (w * v))
 
 
 class BatchEngine:
@@ -111,7 +115,8 @@ def autotune(cases, storage="f16", steps=20, candidates=None, use_cache=True, ve
     (layout, warps_per_block, blocks_per_sm) and returns the fastest as a dict
     with its measured ms per step.  Results are cached per (storage, size class)."""
     import torch
-    key = f"{storage}:{size_class(cases)}"
+    # the key carries the library's ABI version: kernels and limits change with it
+    key = f"abi{B.ABI_VERSION}:{storage}:{size_class(cases)}"
     cache = {}
     if use_cache and os.path.exists(_CACHE):
         try:
@@ -121,7 +126,7 @@ def autotune(cases, storage="f16", steps=20, candidates=None, use_cache=True, ve
         if key in cache:
             return cache[key]
     if candidates is None:
-        candidates = [(lay, w, b) for lay in ("ab", "aa") for w in (2, 4, 8) for b in (0, 1, 2)]
+        candidates = [(lay, w, b) for lay in ("ab", "aa") for w in (1, 2, 4) for b in (0, 1, 2)]
     items = sum(work_items(c.nx, c.ny, storage) for c in cases)
     best = None
     for lay, w, b in candidates:

@@ -50,6 +50,13 @@ olb_status bcuda(cudaError_t e, const char *what) {
 // item groups: (walls, equilibrium kind, collision, parity class)
 constexpr int NGROUPS = 24;
 
+// (walls, equilibrium kind, collision) of a lattice: its batch kernel
+int combo_index(const olb_lattice *L) {
+    const int walls = L->p.boundary == OLB_BOUNDARY_WALLS_X;
+    return (walls * 3 + kernel_eq(&L->p)) * 2 + L->p.coll;
+}
+unsigned combo_bit(const olb_lattice *L) { return 1u << combo_index(L); }
+
 struct Member {
     olb_lattice *lat;
     long long g_base, g_end;  // active global steps [g_base, g_end)
@@ -99,8 +106,7 @@ struct olb_batch {
     int *h_groups;          // pinned, NGROUPS + 1 entries
     long long G;            // global step counter at the start of the next round
     bool captured;
-    bool graph_walls;       // the captured graph launches the wall-column kernels
-    bool graph_local;       // ... and the local-temperature kernels
+    unsigned graph_combos;  // (walls, eq, coll) kernels the captured graph launches
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
@@ -117,14 +123,16 @@ olb_status upload(olb_batch *b) {
         if (L->p.storage == OLB_F64) fill_desc<double>(&b->h_descs[j * b->desc_size], m, L->kd);
         else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf);
         const int cls = (int)((m.t_base - m.g_base) & 1);
-        const int walls = L->p.boundary == OLB_BOUNDARY_WALLS_X;
-        const int eqk = kernel_eq(&L->p);
-        const int grp = ((walls * 3 + eqk) * 2 + L->p.coll) * 2 + cls;
+        const int grp = combo_index(L) * 2 + cls;
         const int lw = segment_log2(L->p.nx, L->V);
         const int segs = (L->p.nx + (L->V << lw) - 1) / (L->V << lw);
-        const int rows = 32 >> lw;  // rows per warp item
-        for (int y = 0; y < L->p.ny; y += rows)
-            for (int s = 0; s < segs; ++s) per_group[grp].push_back(make_int4((int)j, y, s, 0));
+        const int rows = 32 >> lw;  // rows per row group (one warp pass)
+        const int ngroups = (L->p.ny + rows - 1) / rows;
+        for (int q = 0; q < ngroups; q += BATCH_ITEM_ROW_GROUPS) {
+            const int count = std::min(BATCH_ITEM_ROW_GROUPS, ngroups - q);
+            for (int s = 0; s < segs; ++s)
+                per_group[grp].push_back(make_int4((int)j, q * rows, s, count));
+        }
     }
     b->h_items.clear();
     for (int q = 0; q < NGROUPS; ++q) {
@@ -163,12 +171,8 @@ olb_status capture(olb_batch *b) {
     a.grid = b->grid;
     a.block = b->block;
     a.stream = b->stream;
-    a.walls = 0;
-    a.local_theta = 0;
-    for (const Member &m : b->members) {
-        if (m.lat->p.boundary == OLB_BOUNDARY_WALLS_X) a.walls = 1;
-        if (kernel_eq(&m.lat->p) == EQ_GUIDED_LOCAL) a.local_theta = 1;
-    }
+    a.combos = 0;
+    for (const Member &m : b->members) a.combos |= combo_bit(m.lat);
     B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
            "beginning graph capture");
     cudaError_t e = cudaSuccess;
@@ -190,8 +194,7 @@ olb_status capture(olb_batch *b) {
     b->graph = g;
     B_CUDA(cudaGraphInstantiate(&b->exec, g, 0), "instantiating batch graph");
     b->captured = true;
-    b->graph_walls = a.walls != 0;
-    b->graph_local = a.local_theta != 0;
+    b->graph_combos = a.combos;
     return OLB_OK;
 }
 
@@ -211,9 +214,9 @@ olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out) {
         return bfail(OLB_ERR_INVALID, "max_lattices and max_items must be >= 1");
     if (p->steps_per_launch < 1 || p->steps_per_launch > 10000)
         return bfail(OLB_ERR_INVALID, "steps_per_launch must be in [1, 10000]");
-    if (p->warps_per_block < 1 || p->warps_per_block > 8 ||
+    if (p->warps_per_block < 1 || 32 * p->warps_per_block > BATCH_MAX_THREADS ||
         (p->warps_per_block & (p->warps_per_block - 1)))
-        return bfail(OLB_ERR_INVALID, "warps_per_block must be 1, 2, 4 or 8");
+        return bfail(OLB_ERR_INVALID, "warps_per_block must be 1, 2 or 4");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32)
         return bfail(OLB_ERR_INVALID, "blocks_per_sm must be in [0, 32] (0 = occupancy limit)");
     olb_batch *b = new (std::nothrow) olb_batch();
@@ -285,9 +288,7 @@ olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps) {
         return st;
     }
     lat->batch = b;
-    const bool needs_walls = lat->p.boundary == OLB_BOUNDARY_WALLS_X && !b->graph_walls;
-    const bool needs_local = kernel_eq(&lat->p) == EQ_GUIDED_LOCAL && !b->graph_local;
-    if (b->captured && (needs_walls || needs_local)) {
+    if (b->captured && !(b->graph_combos & combo_bit(lat))) {
         // the graph lacks this lattice's kernels: capture again on the next run
         cudaGraphExecDestroy(b->exec);
         cudaGraphDestroy(b->graph);

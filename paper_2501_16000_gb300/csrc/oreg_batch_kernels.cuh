@@ -43,17 +43,19 @@ template <typename C> struct BatchDesc {
 // time parity (g + c) & 1.  Each kernel below handles one (walls, eq, coll)
 // and, for the in-place layout, one parity: one item body per kernel keeps
 // register use at the single-lattice kernels' level.  groups[0..24] are the
-// item offsets of the 24 groups; the bounce-back (walls) and local-temperature
-// kernels are only launched by batches that hold such a lattice.
+// item offsets of the 24 groups.  A batch launches only the kernels of the
+// (walls, eq, coll) combinations its members use (bit ((walls * 3 + eq) * 2
+// + coll) of BatchLaunch::combos).
 enum { BATCH_AB = 0, BATCH_AA_EVEN = 1, BATCH_AA_ODD = 2 };
 
-// 256 threads x 2 blocks per SM caps registers at 128 per thread: the
-// per-lattice constants come from the descriptor in global memory rather than
-// the parameter bank, and left to itself the compiler keeps them all in
-// registers (150-180 for half storage), halving occupancy; reloading a few
-// from L1 is cheaper (measured: 49 -> 63 GLUPS on 512 mixed FP16 lattices).
+// At most 128 threads x 3 blocks per SM: the per-lattice constants come from
+// the descriptor in global memory rather than the parameter bank, and left to
+// itself the compiler keeps them all in registers (150-180 for half storage),
+// halving occupancy.  Measured on 512 mixed FP16 lattices: unbounded 78,
+// 128 registers (256 x 2) 88, 170 registers (128 x 3) 90 GLUPS.
+constexpr int BATCH_MAX_THREADS = 128;
 template <int S, int KIND, int EQ, int COLL, bool WALLS>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, 3)
     k_batch_step(const BatchDesc<typename Storage<S>::C> *__restrict__ descs,
                  const int4 *__restrict__ items, const int *__restrict__ groups,
                  const long long *__restrict__ g_round, int k) {
@@ -72,50 +74,53 @@ __global__ void __launch_bounds__(256, 2)
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int w = lo + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < hi; w += warps) {
+        // item: (lattice, first row, segment, row groups)
         const int4 it = items[w];
         const BatchDesc<typename Storage<S>::C> &d = descs[it.x];
         if (g < d.g_base || g >= d.g_end) continue;  // warp-uniform
         const long long t = d.t_base + (g - d.g_base);
         T *base = static_cast<T *>(d.mem);
-        if constexpr (KIND == BATCH_AB) {
-            const T *src = base + (size_t)(t & 1) * d.buf_elems;
-            T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
-            item_ab<S, EQ, COLL, false, WALLS>(src, dst, d.nx, d.ny, d.pitch, d.plane, it.y, it.z,
-                                               lane, d.lw, d.k, t, d.sr != 0);
-        } else if constexpr (KIND == BATCH_AA_ODD) {
-            item_aa_odd<S, EQ, COLL, false, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, it.y, it.z,
-                                                   lane, d.lw, d.k, t, d.sr != 0);
-        } else {
-            item_aa_even<S, EQ, COLL, false, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, it.y,
-                                                    it.z, lane, d.lw, d.k, t, d.sr != 0);
+        const int rows = 32 >> d.lw;
+        for (int q = 0; q < it.w; ++q) {
+            const int y0 = it.y + q * rows;
+            if constexpr (KIND == BATCH_AB) {
+                const T *src = base + (size_t)(t & 1) * d.buf_elems;
+                T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
+                item_ab<S, EQ, COLL, false, WALLS>(src, dst, d.nx, d.ny, d.pitch, d.plane, y0,
+                                                   it.z, lane, d.lw, d.k, t, d.sr != 0);
+            } else if constexpr (KIND == BATCH_AA_ODD) {
+                item_aa_odd<S, EQ, COLL, false, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
+                                                       it.z, lane, d.lw, d.k, t, d.sr != 0);
+            } else {
+                item_aa_even<S, EQ, COLL, false, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
+                                                        it.z, lane, d.lw, d.k, t, d.sr != 0);
+            }
         }
     }
 }
 
 template <int S> struct BatchLaunchT {
+    template <int KIND, bool WALLS, int EQ, int COLL>
+    static void launch_one(const BatchLaunch &a) {
+        constexpr int bit = ((WALLS ? 1 : 0) * 3 + EQ) * 2 + COLL;
+        if (!(a.combos & (1u << bit))) return;
+        using D = BatchDesc<typename Storage<S>::C>;
+        k_batch_step<S, KIND, EQ, COLL, WALLS><<<a.grid, a.block, 0, a.stream>>>(
+            static_cast<const D *>(a.descs), a.items, a.groups, a.g, a.k);
+    }
     template <int KIND, bool WALLS>
     static void launch_combos(const BatchLaunch &a) {
-        using D = BatchDesc<typename Storage<S>::C>;
-        const D *descs = static_cast<const D *>(a.descs);
-        k_batch_step<S, KIND, EQ_GUIDED, COLL_OREG, WALLS><<<a.grid, a.block, 0, a.stream>>>(
-            descs, a.items, a.groups, a.g, a.k);
-        k_batch_step<S, KIND, EQ_GUIDED, COLL_BGK, WALLS><<<a.grid, a.block, 0, a.stream>>>(
-            descs, a.items, a.groups, a.g, a.k);
-        k_batch_step<S, KIND, EQ_POLY2, COLL_OREG, WALLS><<<a.grid, a.block, 0, a.stream>>>(
-            descs, a.items, a.groups, a.g, a.k);
-        k_batch_step<S, KIND, EQ_POLY2, COLL_BGK, WALLS><<<a.grid, a.block, 0, a.stream>>>(
-            descs, a.items, a.groups, a.g, a.k);
-        if (a.local_theta) {
-            k_batch_step<S, KIND, EQ_GUIDED_LOCAL, COLL_OREG, WALLS><<<a.grid, a.block, 0, a.stream>>>(
-                descs, a.items, a.groups, a.g, a.k);
-            k_batch_step<S, KIND, EQ_GUIDED_LOCAL, COLL_BGK, WALLS><<<a.grid, a.block, 0, a.stream>>>(
-                descs, a.items, a.groups, a.g, a.k);
-        }
+        launch_one<KIND, WALLS, EQ_GUIDED, COLL_OREG>(a);
+        launch_one<KIND, WALLS, EQ_GUIDED, COLL_BGK>(a);
+        launch_one<KIND, WALLS, EQ_POLY2, COLL_OREG>(a);
+        launch_one<KIND, WALLS, EQ_POLY2, COLL_BGK>(a);
+        launch_one<KIND, WALLS, EQ_GUIDED_LOCAL, COLL_OREG>(a);
+        launch_one<KIND, WALLS, EQ_GUIDED_LOCAL, COLL_BGK>(a);
     }
     template <int KIND>
     static cudaError_t launch_kind(const BatchLaunch &a) {
         launch_combos<KIND, false>(a);
-        if (a.walls) launch_combos<KIND, true>(a);
+        launch_combos<KIND, true>(a);
         return cudaGetLastError();
     }
     static cudaError_t launch(const BatchLaunch &a) {

@@ -94,6 +94,11 @@ OREG_DECLARE_LAUNCHERS(f16)
 OREG_DECLARE_LAUNCHERS(bf16)
 
 // One launch of the batched stream-collide kernel (see oreg_batch_kernels.cuh).
+// Row groups (32/W rows of one W-lane segment each) per batched work item: a
+// warp takes up to this many consecutive row groups of one lattice segment,
+// reading the lattice's descriptor once.
+constexpr int BATCH_ITEM_ROW_GROUPS = 4;
+
 struct BatchLaunch {
     const void *descs;        // BatchDesc<C>[]
     const int4 *items;        // work items (descriptor, first row, segment), grouped
@@ -101,8 +106,7 @@ struct BatchLaunch {
     const long long *g;       // device: global step counter of this round
     int k;                    // step within the round
     int layout;
-    int walls;                // also launch the bounce-back (wall column) kernels
-    int local_theta;          // also launch the local-temperature kernels
+    unsigned combos;          // kernels to launch: bit ((walls * 3 + eq) * 2 + coll)
     int grid, block;
     cudaStream_t stream;
 };

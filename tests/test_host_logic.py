@@ -62,8 +62,9 @@ def test_work_items_cover_every_node_once(storage, v):
             w = 1
             while w < 32 and w < vecs:
                 w *= 2
-            assert work_items(nx, ny, storage) * 32 * v >= nx * ny
-            assert work_items(nx, ny, storage) == math.ceil(ny / (32 // w)) * math.ceil(nx / (w * v))
+            groups = math.ceil(ny / (32 // w))
+            assert work_items(nx, ny, storage) * 4 * 32 * v >= nx * ny
+            assert work_items(nx, ny, storage) == math.ceil(groups / 4) * math.ceil(nx / (w * v))
 
 
 class _FakeLattice:
