@@ -241,7 +241,9 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"shear{case.nx}x{case.ny}-oreg-guided", "sample": sample},
+        "config": {"workload": f"shear{case.nx}x{case.ny}-oreg-guided-{args.layout}",
+                   "nodes": case.nodes, "theta": case.theta, "tau": case.tau, "u0": case.u0,
+                   "wave": [case.m, case.n], "sample": sample},
         "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
