@@ -450,6 +450,7 @@ olb_status olb_init_shock_tube(olb_lattice *L, double rho_left, double rho_right
 }
 
 olb_status olb_init_fields(olb_lattice *L, const double *rho, const double *ux, const double *uy) {
+    oreg::NvtxRange nvtx_("olb_init_fields");
     olb_status st = check_lattice(L, false);
     if (st != OLB_OK) return st;
     if (!rho || !ux || !uy) return fail(OLB_ERR_INVALID, "field arrays must not be NULL");
@@ -482,6 +483,7 @@ olb_status olb_init_fields(olb_lattice *L, const double *rho, const double *ux, 
 }
 
 olb_status olb_step(olb_lattice *L, int64_t nsteps) {
+    oreg::NvtxRange nvtx_("olb_step");
     olb_status st = check_lattice(L, true);
     if (st != OLB_OK) return st;
     if (L->batch) return fail(OLB_ERR_STATE, "lattice belongs to a batch: it advances with olb_batch_run");
@@ -525,6 +527,7 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
 int64_t olb_time(const olb_lattice *L) { return L ? L->t : -1; }
 
 olb_status olb_moments(olb_lattice *L, double *rho, double *ux, double *uy, double *theta_loc) {
+    oreg::NvtxRange nvtx_("olb_moments");
     olb_status st = check_lattice(L, true);
     if (st != OLB_OK) return st;
     if (!rho || !ux || !uy) return fail(OLB_ERR_INVALID, "rho, ux, uy must not be NULL");
@@ -565,6 +568,7 @@ olb_status olb_moments_device(olb_lattice *L, double *d_rho, double *d_ux, doubl
 }
 
 olb_status olb_get_populations(olb_lattice *L, double *f9) {
+    oreg::NvtxRange nvtx_("olb_get_populations");
     olb_status st = check_lattice(L, true);
     if (st != OLB_OK) return st;
     if (!f9) return fail(OLB_ERR_INVALID, "f9 must not be NULL");
@@ -621,6 +625,7 @@ olb_status olb_get_region(olb_lattice *L, int32_t x0, int32_t y0, int32_t wx, in
 }
 
 olb_status olb_set_populations(olb_lattice *L, const double *f9, int64_t t) {
+    oreg::NvtxRange nvtx_("olb_set_populations");
     olb_status st = check_lattice(L, false);
     if (st != OLB_OK) return st;
     if (!f9) return fail(OLB_ERR_INVALID, "f9 must not be NULL");
@@ -648,6 +653,7 @@ olb_status olb_set_populations(olb_lattice *L, const double *f9, int64_t t) {
 
 olb_status olb_diagnostics(olb_lattice *L, double *mass, double *mom_x, double *mom_y,
                            int64_t *nonfinite) {
+    oreg::NvtxRange nvtx_("olb_diagnostics");
     olb_status st = check_lattice(L, true);
     if (st != OLB_OK) return st;
     ModeSpec mode{};
@@ -665,6 +671,7 @@ olb_status olb_diagnostics(olb_lattice *L, double *mass, double *mom_x, double *
 }
 
 olb_status olb_wave_mode(olb_lattice *L, int32_t m, int32_t n, double *a_sin, double *a_cos) {
+    oreg::NvtxRange nvtx_("olb_wave_mode");
     olb_status st = check_lattice(L, true);
     if (st != OLB_OK) return st;
     if (!a_sin && !a_cos) return fail(OLB_ERR_INVALID, "a_sin and a_cos must not both be NULL");

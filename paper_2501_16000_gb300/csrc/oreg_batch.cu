@@ -311,6 +311,7 @@ olb_status olb_batch_remove(olb_batch *b, olb_lattice *lat) {
 }
 
 olb_status olb_batch_run(olb_batch *b, int64_t nrounds) {
+    NvtxRange nvtx_("olb_batch_run");
     if (!b) return bfail(OLB_ERR_INVALID, "batch is NULL");
     if (nrounds < 0) return bfail(OLB_ERR_INVALID, "nrounds must be >= 0");
     if (!b->captured) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -44,6 +45,15 @@ struct olb_lattice {
 namespace oreg {
 // Records the message of a failed call for olb_last_error() (oreg_api.cu).
 void set_last_error_message(const char *msg);
+
+// NVTX range over one C-ABI call (visible in Nsight timelines; a no-op when
+// no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Equilibrium kind of the stream-collide kernels for a lattice.
 inline int kernel_eq(const olb_params *p) {

@@ -111,3 +111,40 @@ def test_batch_membership_rules():
         a.step(1)                                  # free again after removal
         assert a.time == 9
         a.close()
+
+
+def test_nonfinite_member_stays_isolated():
+    """A NaN planted in one member's populations spreads only through that
+    lattice: the other members of the batch end bitwise equal to their runs
+    alone, and the poisoned one reports its non-finite nodes."""
+    from paper_2501_16000_gb300 import binding as B
+    from paper_2501_16000_gb300.batch import BatchEngine
+    from paper_2501_16000_gb300.engine import Lattice
+    cases = [W.LatticeCase(nx=61, ny=40, tau=0.7, m=1, n=2, steps=60),
+             W.LatticeCase(nx=96, ny=33, tau=0.8, m=2, n=1, steps=60),
+             W.LatticeCase(nx=45, ny=70, tau=0.6, case="shock", x_split=20, steps=60)]
+    alone = {}
+    for j in (0, 2):
+        c = cases[j]
+        with Lattice(c.nx, c.ny, c.tau, c.theta, storage="f16", layout="aa") as lat:
+            lat.init_case(c)
+            lat.step(c.steps)
+            alone[j] = lat.populations()
+    with BatchEngine("f16", "aa", max_lattices=4, max_items=1 << 12, steps_per_launch=20) as eng:
+        lats = [eng.new_lattice(c) for c in cases]
+        f = lats[1].populations()
+        f[4, 10, 30] = np.nan
+        lats[1].set_populations(f)
+        for lat, c in zip(lats, cases):
+            eng.add(lat, c.steps)
+        eng.run(3)
+        eng.wait()
+        for j in (0, 2):
+            assert np.array_equal(lats[j].populations(), alone[j])
+            assert lats[j].diagnostics()["nonfinite"] == 0
+        with pytest.raises(B.OregError) as e:
+            lats[1].diagnostics()
+        assert e.value.status == B.OLB_ERR_NONFINITE
+        assert lats[1].diagnostics(raise_nonfinite=False)["nonfinite"] > 100
+        for lat in lats:
+            lat.close()
