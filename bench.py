@@ -390,7 +390,7 @@ def run_native(args):
 
 
 def batched_section(args):
-    """Config 4: 512 independent uneven lattices, FP16 storage (stochastic
+    """Batched workload: 512 independent uneven lattices, FP16 storage (stochastic
     rounding) / FP32 compute, autotuned batch, one CUDA-graph replay per 100
     steps; against serial plain FP32 single-lattice solves of the same set."""
     import numpy as np
@@ -461,7 +461,7 @@ def batched_section(args):
 
 
 def serving_section(args, batched):
-    """Config 5: Poisson arrivals at ~80% of the measured batched capacity,
+    """Serving workload: Poisson arrivals at ~80% of the measured batched capacity,
     sides 64..2048, steps 100..10000, admission against a 120 GB budget,
     continuous batching (FP16, stochastic rounding); vs serial FP32 solves."""
     import numpy as np

@@ -61,26 +61,26 @@ def rel_linf(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-CONFIG1 = [W.shear_64("oreg"), W.shear_64("bgk"), W.shear_64("oreg", 1, 1)]
-CONFIG2 = [W.shock_2048x4("guided"), W.shock_2048x4("poly2")]
+SHEAR_64 = [W.shear_64("oreg"), W.shear_64("bgk"), W.shear_64("oreg", 1, 1)]
+SHOCK_2048X4 = [W.shock_2048x4("guided"), W.shock_2048x4("poly2")]
 
 
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-@pytest.mark.parametrize("case", CONFIG1, ids=lambda c: f"shear64-{c.coll}-{c.m}{c.n}")
-def test_config1_shear_wave_fp64(case, layout):
+@pytest.mark.parametrize("case", SHEAR_64, ids=lambda c: f"shear64-{c.coll}-{c.m}{c.n}")
+def test_shear_wave_64x64_fp64(case, layout):
     err = rel_linf(gpu_run(case, case.steps, "f64", layout), oracle_run(case, case.steps))
     assert err <= TOL["f64"], err
 
 
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-@pytest.mark.parametrize("case", CONFIG2, ids=lambda c: f"shock-{c.eq}")
-def test_config2_shock_tube_fp64(case, layout):
+@pytest.mark.parametrize("case", SHOCK_2048X4, ids=lambda c: f"shock-{c.eq}")
+def test_shock_tube_2048x4_fp64(case, layout):
     err = rel_linf(gpu_run(case, case.steps, "f64", layout), oracle_run(case, case.steps))
     assert err <= TOL["f64"], err
 
 
-@pytest.mark.parametrize("case", CONFIG1[:2], ids=lambda c: f"shear64-{c.coll}")
-def test_config1_shear_wave_fp32(case):
+@pytest.mark.parametrize("case", SHEAR_64[:2], ids=lambda c: f"shear64-{c.coll}")
+def test_shear_wave_64x64_fp32(case):
     err = rel_linf(gpu_run(case, case.steps, "f32", "ab"), oracle_run(case, case.steps))
     assert err <= TOL["f32"], err
 
@@ -97,8 +97,8 @@ TOL_F32_SHOCK_2000 = 5e-5
 
 @pytest.mark.parametrize("comp", [0, 1])
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-@pytest.mark.parametrize("case", CONFIG2, ids=lambda c: f"shock-{c.eq}")
-def test_config2_shock_tube_fp32(case, layout, comp):
+@pytest.mark.parametrize("case", SHOCK_2048X4, ids=lambda c: f"shock-{c.eq}")
+def test_shock_tube_2048x4_fp32(case, layout, comp):
     opts = {"comp": comp}
     err = rel_linf(gpu_run(case, case.steps, "f32", layout, **opts), oracle_run(case, case.steps))
     print(f"FP32 shock {case.eq} {layout} comp={comp} t=2000: rel Linf {err:.3e}")
