@@ -87,3 +87,47 @@ def test_bad_enums_and_null_handles(lib):
     assert lib.olb_step(None, 1) == B.OLB_ERR_INVALID
     assert lib.olb_destroy(None) == B.OLB_OK
     assert lib.olb_time(None) == -1
+
+
+def test_header_compiles_as_c_and_struct_layouts_match_the_binding(tmp_path):
+    """include/oreg.h is plain C99 (and C++), and the ctypes mirrors of
+    olb_params / olb_batch_params have the C compiler's sizes and offsets."""
+    fields = {"olb_params": [f[0] for f in B.olb_params._fields_],
+              "olb_batch_params": [f[0] for f in B.olb_batch_params._fields_]}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "oreg.h"', "int main(void) {"]
+    for st, names in fields.items():
+        lines.append(f'    printf("{st} size %zu\\n", sizeof({st}));')
+        for n in names:
+            lines.append(f'    printf("{st} {n} %zu\\n", offsetof({st}, {n}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER),
+                    str(src), "-o", str(exe)], check=True, capture_output=True)
+    subprocess.run(["g++", "-std=c++17", "-fsyntax-only", "-Wall", "-Werror", "-x", "c++",
+                    "-I", os.path.dirname(HEADER), str(src)], check=True, capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        st, name, val = line.split()
+        got[(st, name)] = int(val)
+    for st, cls in (("olb_params", B.olb_params), ("olb_batch_params", B.olb_batch_params)):
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for n in fields[st]:
+            assert got[(st, n)] == getattr(cls, n).offset, (st, n)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(boundary="walls_x", nx=2), dict(eq="poly2", theta_mode="local")])
+def test_invalid_boundary_and_temperature_modes(lib, bad):
+    p = _params(**bad)
+    assert lib.olb_required_bytes(ctypes.byref(p)) == 0
+    h = ctypes.c_void_p()
+    assert lib.olb_create_lattice(ctypes.byref(p), ctypes.byref(h)) == B.OLB_ERR_INVALID
+    p = _params()
+    p.theta_mode = 5
+    assert lib.olb_create_lattice(ctypes.byref(p), ctypes.byref(h)) == B.OLB_ERR_INVALID
+    p = _params()
+    p.boundary = -1
+    assert lib.olb_create_lattice(ctypes.byref(p), ctypes.byref(h)) == B.OLB_ERR_INVALID
