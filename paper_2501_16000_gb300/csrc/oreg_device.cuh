@@ -410,13 +410,29 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         const C X[3] = {-ux, C(1) - ux, C(-1) - ux};
         const C Y[3] = {-uy, C(1) - uy, C(-1) - uy};
         if constexpr (PACKED) {
-            const C asxx = a * sxx, a2sxy = C(2) * a * sxy;
+            // a d_i expanded in c_i (an identity of the contraction below):
+            //   a d_i = A + Sxx (cx^2 - cy^2) + 2 Sxy cx cy - cx P + cy Q, with
+            //   Sxx = a sxx, Sxy = a sxy, A = Sxx (ux^2 - uy^2) + 2 Sxy ux uy,
+            //   P = 2 (Sxx ux + Sxy uy), Q = 2 (Sxx uy - Sxy ux),
+            // so each direction costs one or two additions.
+            const C Sxx = a * sxx, Sxy = a * sxy, Sxy2 = C(2) * Sxy;
+            const C A = fma(Sxx, ux2 - uy2, Sxy2 * (ux * uy));
+            const C P = C(2) * fma(Sxx, ux, Sxy * uy), Q = C(2) * fma(Sxx, uy, -(Sxy * ux));
+            const C Ap = A + Sxx, Am = A - Sxx, Dp = A + Sxy2, Dm = A - Sxy2;
+            C ad[9];
+            ad[0] = A;
+            ad[1] = Ap - P;            // (+1, 0)
+            ad[3] = Ap + P;            // (-1, 0)
+            ad[2] = Am + Q;            // (0, +1)
+            ad[4] = Am - Q;            // (0, -1)
+            ad[5] = (Dp - P) + Q;      // (+1, +1)
+            ad[7] = (Dp + P) - Q;      // (-1, -1)
+            ad[6] = (Dm + P) + Q;      // (-1, +1)
+            ad[8] = (Dm - P) - Q;      // (+1, -1)
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const int ia = kidx(cx_of(i)), ib = kidx(cy_of(i));
-                const C ad = fma(X[ia] * X[ia] - Y[ib] * Y[ib], asxx, X[ia] * Y[ib] * a2sxy);
                 const C feq = k.shift[dcls(i)] + geq[i];
-                post[i] = fma(feq, ad, geq[i]);
+                post[i] = fma(feq, ad[i], geq[i]);
             }
         } else {
             const C two_sxy = C(2) * sxy;
