@@ -131,7 +131,19 @@ typedef enum {
        nearest there changes a shear wave's decay rate by up to ~1e-1 at
        tau = 0.52); results stay deterministic and independent of batching
        and layout.  0: round to nearest even.  Ignored by F32 and F64. */
-    OLB_OPT_STOCHASTIC_ROUNDING = 3
+    OLB_OPT_STOCHASTIC_ROUNDING = 3,
+    /* OLB_F32 storage only.  1: olb_step computes the collision in FP64
+       (decode, Eqs. 6-7, encode) while the populations stay stored in
+       FP32, so the store is the only FP32 rounding of a step.  Over long,
+       weakly damped runs the FP32 collision's own rounding dominates the
+       drift from the FP64 result (2048 x 4 shock tube, tau = 0.51, 2000
+       steps: ~2e-5 relative with the FP32 collision, ~4e-6 from the FP32
+       store alone); this mode is for such accuracy runs, at the GPU's FP64
+       rate (a few GLUPS).  The stored state is that of the FP32 collision
+       (same elements and shifts), so the option may change between steps.
+       0 (default): FP32 collision.  OLB_ERR_INVALID for value 1 on another
+       storage format; olb_batch_add rejects a lattice with it set. */
+    OLB_OPT_F64_COLLISION = 4
 } olb_option;
 
 /* Version of this ABI (bumped on incompatible change); 3 since

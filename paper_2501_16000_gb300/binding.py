@@ -19,6 +19,7 @@ OLB_COLL_OREG, OLB_COLL_BGK = 0, 1
 OLB_F64, OLB_F32, OLB_F16_SHIFTED, OLB_BF16_SHIFTED = 0, 1, 2, 3
 OLB_LAYOUT_AB, OLB_LAYOUT_AA = 0, 1
 OLB_OPT_COMPENSATED, OLB_OPT_WARPS_PER_BLOCK, OLB_OPT_STOCHASTIC_ROUNDING = 1, 2, 3
+OLB_OPT_F64_COLLISION = 4
 
 STATUS_NAMES = {0: "OLB_OK", 1: "OLB_ERR_INVALID", 2: "OLB_ERR_NOMEM", 3: "OLB_ERR_CUDA",
                 4: "OLB_ERR_NONFINITE", 5: "OLB_ERR_TIMEOUT", 6: "OLB_ERR_STATE"}

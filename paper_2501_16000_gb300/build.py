@@ -29,6 +29,7 @@ UNITS = {
     "oreg_st_f32.cu": [],
     "oreg_st_f16.cu": [],
     "oreg_st_bf16.cu": [],
+    "oreg_st_f32c64.cu": [],
     "oreg_batch.cu": [],
     "oreg_noalloc.cu": [],
 }

@@ -327,6 +327,7 @@ olb_status olb_create_lattice(const olb_params *p, olb_lattice **out) {
     L->nbuf = p->layout == OLB_LAYOUT_AB ? 2 : 1;
     L->t = -1;
     L->comp = 0;
+    L->f64_coll = 0;
     L->sr = (p->storage == OLB_F16_SHIFTED || p->storage == OLB_BF16_SHIFTED) ? 1 : 0;
     L->warps_per_block = 4;
     L->kd = make_const_f64_for(p);
@@ -391,6 +392,12 @@ olb_status olb_set_option(olb_lattice *L, int32_t option, int64_t value) {
         case OLB_OPT_STOCHASTIC_ROUNDING:
             if (value != 0 && value != 1) return fail(OLB_ERR_INVALID, "OLB_OPT_STOCHASTIC_ROUNDING takes 0 or 1");
             L->sr = (int)value;
+            return OLB_OK;
+        case OLB_OPT_F64_COLLISION:
+            if (value != 0 && value != 1) return fail(OLB_ERR_INVALID, "OLB_OPT_F64_COLLISION takes 0 or 1");
+            if (value == 1 && L->p.storage != OLB_F32)
+                return fail(OLB_ERR_INVALID, "OLB_OPT_F64_COLLISION needs OLB_F32 storage");
+            L->f64_coll = (int)value;
             return OLB_OK;
         case OLB_OPT_WARPS_PER_BLOCK:
             if (value < 1 || value > 8 || (value & (value - 1)))
@@ -502,8 +509,11 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     a.sr = L->sr;
     a.walls = L->p.boundary == OLB_BOUNDARY_WALLS_X;
     a.warps_per_block = L->warps_per_block;
-    a.kconst = L->p.storage == OLB_F64 ? static_cast<const void *>(&L->kd)
-                                       : static_cast<const void *>(&L->kf);
+    // FP32 storage with the FP64 collision runs on the FP64 constants, whose
+    // shifts are the FP32 storage's (make_const_f64_for)
+    const bool c64 = L->f64_coll && L->p.storage == OLB_F32;
+    a.kconst = L->p.storage == OLB_F64 || c64 ? static_cast<const void *>(&L->kd)
+                                              : static_cast<const void *>(&L->kf);
     a.stream = L->stream;
     const size_t bytes = L->buf_elems * L->esize;
     char *mem = static_cast<char *>(L->mem);
@@ -517,7 +527,7 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
             a.src = mem;
             a.dst = nullptr;
         }
-        cudaError_t e = DISPATCH(L->p.storage, step, a);
+        cudaError_t e = c64 ? step_f32c64(a) : DISPATCH(L->p.storage, step, a);
         if (e != cudaSuccess) return cuda_fail(e, "launching stream-collide");
         L->t += 1;
     }

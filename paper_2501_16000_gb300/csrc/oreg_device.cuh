@@ -45,7 +45,7 @@ static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) ==
 // polynomial, and guided at each node's own temperature (local theta).
 enum { EQ_GUIDED = 0, EQ_POLY2 = 1, EQ_GUIDED_LOCAL = 2 };
 enum { COLL_OREG = 0, COLL_BGK = 1 };
-enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3, ST_F32_C64 = 4 };
 
 // ---------------------------------------------------------------------------
 // Storage traits: T = stored element, C = compute type, V = elements per 16 B.
@@ -76,6 +76,18 @@ template <> struct Storage<ST_F32> {
     __device__ static T enc(C v) { return v; }
     __device__ static C dec_step(T v) { return v; }
     __device__ static T enc_step(C v) { return v; }
+};
+// FP32 storage with the collision in FP64 (option OLB_OPT_F64_COLLISION): the
+// stored elements and shifts are those of ST_F32, so a state written by either
+// kernel is read by the other; the only FP32 rounding left in a step is the
+// store of the post-collision values.
+template <> struct Storage<ST_F32_C64> {
+    using T = float; using C = double; static constexpr int V = 4;
+    static constexpr double STEP_SCALE = 1.0;
+    __device__ static C dec(T v) { return v; }
+    __device__ static T enc(C v) { return __double2float_rn(v); }
+    __device__ static C dec_step(T v) { return v; }
+    __device__ static T enc_step(C v) { return __double2float_rn(v); }
 };
 // Half formats also offer stochastic rounding: the bits of v below the
 // format's last mantissa bit (13 for f16, 16 for bf16) get uniform random

@@ -27,6 +27,7 @@ struct olb_lattice {
     int64_t t;            // time of the canonical state; -1 = uninitialised
     int comp;
     int sr;               // stochastic rounding of half formats
+    int f64_coll;         // FP32 storage: collision in FP64 (OLB_OPT_F64_COLLISION)
     int warps_per_block;
     int num_sms;
     double *d_red;        // reduction partials + result (library scratch)

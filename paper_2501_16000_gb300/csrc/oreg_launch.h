@@ -92,6 +92,10 @@ OREG_DECLARE_LAUNCHERS(f64)
 OREG_DECLARE_LAUNCHERS(f32)
 OREG_DECLARE_LAUNCHERS(f16)
 OREG_DECLARE_LAUNCHERS(bf16)
+// Stream-collide only, FP32 storage with the FP64 collision (ST_F32_C64); the
+// state is that of FP32 storage, so initialisation, readback and reductions
+// use the f32 launchers.
+cudaError_t step_f32c64(const StepArgs &a);
 
 // One launch of the batched stream-collide kernel (see oreg_batch_kernels.cuh).
 // Row groups (32/W rows of one W-lane segment each) per batched work item: a

@@ -131,3 +131,26 @@ def test_invalid_boundary_and_temperature_modes(lib, bad):
     p = _params()
     p.boundary = -1
     assert lib.olb_create_lattice(ctypes.byref(p), ctypes.byref(h)) == B.OLB_ERR_INVALID
+
+
+def test_header_enum_values_match_the_binding(tmp_path):
+    """Every status, equilibrium, collision, storage, layout and option value
+    the binding passes is the value the C compiler sees in include/oreg.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    names = re.findall(r"\b(OLB_[A-Z0-9_]+)\s*=", text)
+    lines = ["#include <stdio.h>", '#include "oreg.h"', "int main(void) {"]
+    lines += [f'    printf("{n} %d\\n", (int){n});' for n in names]
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(line.split() for line in subprocess.run(
+        [str(exe)], check=True, capture_output=True, text=True).stdout.splitlines())
+    mapped = {"OLB_BOUNDARY_PERIODIC": B.BOUNDARY["periodic"],
+              "OLB_BOUNDARY_WALLS_X": B.BOUNDARY["walls_x"],
+              "OLB_THETA_FIXED": B.THETA_MODE["fixed"], "OLB_THETA_LOCAL": B.THETA_MODE["local"]}
+    for n in names:
+        want = mapped[n] if n in mapped else getattr(B, n)
+        assert int(got[n]) == want, n

@@ -148,3 +148,23 @@ def test_nonfinite_member_stays_isolated():
         assert lats[1].diagnostics(raise_nonfinite=False)["nonfinite"] > 100
         for lat in lats:
             lat.close()
+
+
+def test_batch_rejects_a_lattice_with_the_fp64_collision():
+    """OLB_OPT_F64_COLLISION is a single-lattice mode: olb_batch_add refuses
+    such a lattice, and accepts it once the option is off again."""
+    from paper_2501_16000_gb300 import binding as B
+    from paper_2501_16000_gb300.batch import BatchEngine
+    with BatchEngine("f32", "ab", max_lattices=4, max_items=1 << 12, steps_per_launch=4,
+                     warps_per_block=4) as eng:
+        lat = eng.new_lattice(W.shear_64("oreg"))
+        lat.set_option(B.OLB_OPT_F64_COLLISION, 1)
+        with pytest.raises(B.OregError) as e:
+            eng.add(lat, 8)
+        assert e.value.status == B.OLB_ERR_INVALID
+        lat.set_option(B.OLB_OPT_F64_COLLISION, 0)
+        eng.add(lat, 8)
+        eng.run(3)
+        eng.wait()
+        assert lat.time == 8 and eng.remaining(lat) == 0
+        lat.close()
