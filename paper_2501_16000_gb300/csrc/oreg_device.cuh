@@ -143,11 +143,13 @@ template <> struct Storage<ST_BF16> {
 
 // Counter-based random bits for stochastic rounding: one hash per node pair
 // (x, x+1), x even, and time step (the 32-bit finalizer of MurmurHash3 of
-// (x/2, y, t)), then one multiplicative hash per direction, r = h * M_i with
-// distinct odd M_i, folded as r ^ (r >> 16) so that both 16-bit halves
-// (the low half feeds node x, the high half node x+1) depend on every bit of
-// h.  The draws depend only on (x, y, t, i), so results do not depend on how
-// nodes are scheduled, batched or laid out.
+// (x/2, y, t)), then the nine directions' words as an arithmetic progression
+// r_i = h + i d (mod 2^32) with an odd step d mixed from h, one addition per
+// direction.  The low 16-bit half of r_i feeds node x, the high half node
+// x+1.  Each r_i is uniform when h is (so the rounding stays unbiased), and
+// for i != j the difference (i - j) d is itself random.  The draws depend
+// only on (x, y, t, i), so results do not depend on how nodes are scheduled,
+// batched or laid out.
 __device__ __forceinline__ uint32_t node_seed(int x, int y, long long t) {
     uint32_t h = (uint32_t)x * 0x9E3779B1u;
     h ^= (uint32_t)y * 0x85EBCA77u + 0x632BE5ABu;
@@ -159,14 +161,8 @@ __device__ __forceinline__ uint32_t node_seed(int x, int y, long long t) {
     h ^= h >> 16;
     return h;
 }
-__device__ __forceinline__ uint32_t direction_mult(int i) {
-    const uint32_t m[9] = {0x9E3779B9u, 0x7F4A7C15u, 0xF39CC061u, 0x5851F42Du, 0xC8E2D8F5u,
-                           0x2545F491u, 0xB5297A4Du, 0x68E31DA5u, 0x1B56C4E9u};
-    return m[i];
-}
-__device__ __forceinline__ uint32_t pair_bits(uint32_t h, int i) {
-    const uint32_t r = h * direction_mult(i);
-    return r ^ (r >> 16);
+__device__ __forceinline__ uint32_t pair_step(uint32_t h) {
+    return ((h ^ (h >> 15)) * 0x2C1B3C6Du) | 1u;
 }
 
 // 16-byte vector of V stored elements.
@@ -382,6 +378,9 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         const C qx = C(0.5) * ux, hx = C(0.5) * ex2, qy = C(0.5) * uy, hy = C(0.5) * ey2;
         const C dpx[3] = {-ex2, hx + qx, hx - qx};
         const C dpy[3] = {-ey2, hy + qy, hy - qy};
+        C c3[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) c3[c] = fma(drho, k.w_lo[c], k.corr[c]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
@@ -390,8 +389,7 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
             const C psib = k.psi0[pb] + dpy[b];
             const C t = fma(dpx[a], psib,
                             fma(dpx[a], k.psi0_lo[pb], fma(k.psi0[pa], dpy[b], k.psi0_lo[pa] * dpy[b])));
-            const C vel = fma(rho, t, k.corr[ci]);
-            geq[i] = fma(drho, k.w[ci], fma(drho, k.w_lo[ci], vel));
+            geq[i] = fma(drho, k.w[ci], fma(rho, t, c3[ci]));
         }
     } else {
         const C u2 = ux2 + uy2;

@@ -9,6 +9,14 @@
 
 namespace oreg {
 
+// Blocks of the largest size (256 threads) that the stream-collide kernels
+// must fit per SM: 2 for the half formats caps them at 128 registers, so that
+// 16 warps stay resident (the issue-bound half formats need them; the odd AA
+// step would otherwise take ~140 registers and drop to 12 warps).
+__host__ __device__ constexpr int step_min_blocks(int S) {
+    return S == ST_F16 || S == ST_BF16 ? 2 : 1;
+}
+
 // ---------------------------------------------------------------------------
 // Stream-collide, A-B layout.  A buffer holds post-collision populations at
 // the node that produced them.  A warp gathers, for 32*V nodes of one row,
@@ -71,7 +79,7 @@ __device__ __forceinline__ void zero_padding(typename Storage<S>::C f[9][Storage
 // time step and direction.
 // Half formats encode node pairs (x, x+1), x even, with one packed
 // conversion; the stochastic draws of a pair and direction i are
-// pair_bits(node_seed(x / 2, y, t), i).
+// h + i pair_step(h), h = node_seed(x / 2, y, t).
 template <int S>
 __device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Storage<S>::V],
                                            typename Storage<S>::T e[9][Storage<S>::V], int xb,
@@ -83,10 +91,13 @@ __device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Sto
         if (sr) {
 #pragma unroll
             for (int j = 0; j < ST::V; j += 2) {
-                const uint32_t h = node_seed((xb + j) >> 1, y, t);
+                const uint32_t h = node_seed((xb + j) >> 1, y, t), d = pair_step(h);
+                uint32_t r = h;
 #pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    w[i][j / 2] = ST::enc2_stochastic(f[i][j], f[i][j + 1], pair_bits(h, i));
+                for (int i = 0; i < 9; ++i) {
+                    w[i][j / 2] = ST::enc2_stochastic(f[i][j], f[i][j + 1], r);
+                    r += d;
+                }
             }
         } else {
 #pragma unroll
@@ -379,7 +390,7 @@ __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, i
 }
 
 template <int S, int EQ, int COLL, bool COMP, bool WALLS>
-__global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
+__global__ void __launch_bounds__(256, step_min_blocks(S)) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
                                                      int pitch, size_t plane, int segs, int lw,
                                                      const CollConst<typename Storage<S>::C> k,
                                                      long long t, bool sr) {
