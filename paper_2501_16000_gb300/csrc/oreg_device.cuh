@@ -378,9 +378,12 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         const C qx = C(0.5) * ux, hx = C(0.5) * ex2, qy = C(0.5) * uy, hy = C(0.5) * ey2;
         const C dpx[3] = {-ex2, hx + qx, hx - qx};
         const C dpy[3] = {-ey2, hy + qy, hy - qy};
+        // packed (issue-bound) path: drho W_lo + corr once per symmetry class;
+        // the scalar path keeps it per direction (fewer live registers, which
+        // the HBM-bound FP32 in-place kernels need for occupancy)
         C c3[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) c3[c] = fma(drho, k.w_lo[c], k.corr[c]);
+        for (int c = 0; c < 3; ++c) c3[c] = PACKED ? fma(drho, k.w_lo[c], k.corr[c]) : k.corr[c];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
@@ -389,7 +392,12 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
             const C psib = k.psi0[pb] + dpy[b];
             const C t = fma(dpx[a], psib,
                             fma(dpx[a], k.psi0_lo[pb], fma(k.psi0[pa], dpy[b], k.psi0_lo[pa] * dpy[b])));
-            geq[i] = fma(drho, k.w[ci], fma(rho, t, c3[ci]));
+            if constexpr (PACKED) {
+                geq[i] = fma(drho, k.w[ci], fma(rho, t, c3[ci]));
+            } else {
+                const C vel = fma(rho, t, k.corr[ci]);
+                geq[i] = fma(drho, k.w[ci], fma(drho, k.w_lo[ci], vel));
+            }
         }
     } else {
         const C u2 = ux2 + uy2;

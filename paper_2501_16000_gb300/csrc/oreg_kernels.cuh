@@ -9,12 +9,19 @@
 
 namespace oreg {
 
-// Blocks of the largest size (256 threads) that the stream-collide kernels
-// must fit per SM: 2 for the half formats caps them at 128 registers, so that
-// 16 warps stay resident (the issue-bound half formats need them; the odd AA
-// step would otherwise take ~140 registers and drop to 12 warps).
+// Blocks of the largest size (256 threads) that the capped odd AA step must
+// fit per SM, which caps its registers: 2 for the half formats (128
+// registers, 16 warps resident; the issue-bound half formats need them, and
+// the kernel would otherwise take ~140 registers), 3 for FP32 (85 registers,
+// 24 warps for the HBM-bound kernel).  The periodic fixed-temperature kernels
+// of these formats use the capped kernel; the wall and local-temperature
+// variants need more registers and keep the compiler's own choice.
 __host__ __device__ constexpr int step_min_blocks(int S) {
-    return S == ST_F16 || S == ST_BF16 ? 2 : 1;
+    return S == ST_F16 || S == ST_BF16 ? 2 : 3;
+}
+template <int S, int EQ, bool WALLS>
+__host__ __device__ constexpr bool aa_odd_capped() {
+    return !WALLS && EQ != EQ_GUIDED_LOCAL && (S == ST_F16 || S == ST_BF16 || S == ST_F32);
 }
 
 // ---------------------------------------------------------------------------
@@ -389,18 +396,29 @@ __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, i
     push_plane<S, 8>(A, plane, pitch, y, ny, xb, nx, sub, W, e[8]);
 }
 
+#define OREG_AA_ODD_BODY                                                                    \
+    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  \
+    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);                                   \
+    if (item >= (long long)groups * segs) return;                                           \
+    item_aa_odd<S, EQ, COLL, COMP, WALLS>(A, nx, ny, pitch, plane,                          \
+                                          (int)(item / segs) << (5 - lw), (int)(item % segs), \
+                                          threadIdx.x & 31, lw, k, t, sr);
+
 template <int S, int EQ, int COLL, bool COMP, bool WALLS>
-__global__ void __launch_bounds__(256, step_min_blocks(S)) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
+__global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
                                                      int pitch, size_t plane, int segs, int lw,
                                                      const CollConst<typename Storage<S>::C> k,
                                                      long long t, bool sr) {
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
-    if (item >= (long long)groups * segs) return;
-    item_aa_odd<S, EQ, COLL, COMP, WALLS>(A, nx, ny, pitch, plane,
-                                          (int)(item / segs) << (5 - lw), (int)(item % segs),
-                                          threadIdx.x & 31, lw, k, t, sr);
+    OREG_AA_ODD_BODY
 }
+template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+__global__ void __launch_bounds__(256, step_min_blocks(S))
+    k_step_aa_odd_capped(typename Storage<S>::T *A, int nx, int ny, int pitch, size_t plane,
+                         int segs, int lw, const CollConst<typename Storage<S>::C> k, long long t,
+                         bool sr) {
+    OREG_AA_ODD_BODY
+}
+#undef OREG_AA_ODD_BODY
 
 // ---------------------------------------------------------------------------
 // Launcher
@@ -423,9 +441,15 @@ template <int S> struct StepLaunch {
                 static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
                 a.sr != 0);
         } else {
-            k_step_aa_odd<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
-                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
-                a.sr != 0);
+            if constexpr (aa_odd_capped<S, EQ, WALLS>()) {
+                k_step_aa_odd_capped<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
+                    static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
+                    a.sr != 0);
+            } else {
+                k_step_aa_odd<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
+                    static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
+                    a.sr != 0);
+            }
         }
     }
 
