@@ -194,13 +194,15 @@ def mach_wave(geometry: str, mach: float, coll: str = "oreg", nu: float = 0.01,
     ``axis``: u_x = A0 sin(2 pi y / L) on a 4 x L lattice, wave vector along y.
     ``diagonal``: the pi/4 wave, u = (A0, A0) sin(k . x) with k along (-1, 1) on
     an M x M lattice, M = round(L sqrt 2), so the wavelength is L as in the
-    axis case.  tau = 1/2 + nu / theta."""
+    axis case.  tau = 1/2 + nu / theta.  The shear-wave fields point along
+    e_perp = (-k_y, k_x) / |k|, which is -x (axis) and -(1, 1) / sqrt 2
+    (diagonal) here, so the amplitudes are negated to give the paper's signs."""
     tau = 0.5 + nu / theta
     if geometry == "axis":
-        nx, ny, m, n, u0 = 4, length, 0, 1, amplitude
+        nx, ny, m, n, u0 = 4, length, 0, 1, -amplitude
     elif geometry == "diagonal":
         side = int(round(length * math.sqrt(2.0)))
-        nx, ny, m, n, u0 = side, side, -1, 1, amplitude * math.sqrt(2.0)
+        nx, ny, m, n, u0 = side, side, -1, 1, -amplitude * math.sqrt(2.0)
     else:
         raise ValueError(f"unknown geometry {geometry!r}")
     return LatticeCase(nx=nx, ny=ny, tau=tau, theta=theta, coll=coll, case="shear", u0=u0,

@@ -129,3 +129,43 @@ def test_serving_admission_fifo_and_budget():
         assert r.done_s >= r.admitted_s >= r.arrival_s - 1e-9 and r.latency_s >= 0
         assert r.fields[0].shape == (next(q.lattice.ny for q in trace if q.rid == r.rid),
                                      next(q.lattice.nx for q in trace if q.rid == r.rid))
+
+
+def test_paper_workloads_use_the_printed_parameters():
+    """The Sec. IV workloads are built from the values the paper prints
+    (tests/golden/paper_values.json): the walled shock tube's grid, steps,
+    temperatures and viscosities, and the shear wave's amplitude, length,
+    temperature and viscosity.  The axis-aligned wave runs 4 columns wide
+    instead of the printed 1 (the wave does not vary in x, so the columns
+    are identical)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_values.json")
+    g = json.load(open(path))
+    s = g["walled_shock_tube"]
+    for gc in s["cases"]:
+        c = W.shock_tube_walls(theta=gc["theta"], nu=gc["nu"])
+        assert [c.nx, c.ny] == s["grid"] and c.steps == s["steps"]
+        assert c.boundary == "walls_x" and c.eq == "guided"
+        assert abs(c.theta * (c.tau - 0.5) - gc["nu"]) <= 1e-15
+    d = g["decaying_shear_wave"]
+    theta = d["theta"][0] / d["theta"][1]
+    for ma in (0.0, 0.2, 0.4):
+        c = W.mach_wave("axis", ma)
+        assert c.ny == d["grid"][1] and (c.m, c.n) == (0, 1)
+        assert abs(c.u0) == d["A0"] and abs(c.theta - theta) <= 1e-15
+        assert abs(c.theta * (c.tau - 0.5) - d["nu"]) <= 1e-15
+        assert abs(c.uy_mean - ma * math.sqrt(theta)) <= 1e-15
+        x, y = np.meshgrid(np.arange(c.nx), np.arange(c.ny))
+        rho, ux, uy = c.fields()
+        assert np.allclose(rho, d["rho0"])
+        assert np.allclose(ux, d["A0"] * np.sin(2 * np.pi * y / d["grid"][1]), rtol=0, atol=1e-15)
+        assert np.allclose(uy, c.uy_mean, rtol=0, atol=1e-15)
+    # the pi/4 wave: u = (A0, A0 + Ma sqrt(theta)) with sin(2 pi (-x + y) / (L sqrt 2))
+    c = W.mach_wave("diagonal", 0.2)
+    x, y = np.meshgrid(np.arange(c.nx), np.arange(c.ny))
+    rho, ux, uy = c.fields()
+    s = d["A0"] * np.sin(2 * np.pi * (-x + y) / c.nx)
+    assert c.nx == round(d["grid"][1] * math.sqrt(2))
+    assert np.allclose(ux, s, rtol=0, atol=1e-15)
+    assert np.allclose(uy, c.uy_mean + s, rtol=0, atol=1e-15)
