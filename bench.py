@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--warps", type=int, default=4, help="OLB_OPT_WARPS_PER_BLOCK")
     ap.add_argument("--sr", type=int, default=None,
                     help="OLB_OPT_STOCHASTIC_ROUNDING for f16/bf16 (library default: 1)")
+    ap.add_argument("--f64-collision", type=int, default=0,
+                    help="OLB_OPT_F64_COLLISION (FP32 storage, collision in FP64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extended", action="store_true",
                     help="skip the batched, serving and precision sections")
@@ -275,6 +277,8 @@ def run_native(args):
     lat.set_option(B.OLB_OPT_WARPS_PER_BLOCK, args.warps)
     if args.sr is not None:
         lat.set_option(B.OLB_OPT_STOCHASTIC_ROUNDING, args.sr)
+    if args.f64_collision:
+        lat.set_option(B.OLB_OPT_F64_COLLISION, args.f64_collision)
     lat.init_case(case)
 
     def barrier():
@@ -320,7 +324,8 @@ def run_native(args):
     bpn = bytes_per_node_step(args.storage)
     peak, peak_kind = measured_peaks()
     achieved = bpn * N / (kern_ms / 1e3) / 1e9
-    kernel_key = f"step_{args.layout}_{args.storage}_guided_oreg_{case.nx}x{case.ny}"
+    kernel_key = (f"step_{args.layout}_{args.storage}{'_c64' if args.f64_collision else ''}"
+                  f"_guided_oreg_{case.nx}x{case.ny}")
     traffic = profiled_traffic(kernel_key)
 
     # end to end through the public API: host fields (pinned) in, moments out
@@ -370,6 +375,8 @@ def run_native(args):
                        "wave": [case.m, case.n], "storage": args.storage,
                        "layout": args.layout, "diagnostics_every": DIAG_EVERY,
                        "compensated": args.comp, "warps_per_block": args.warps,
+                       "collision": "f64" if args.f64_collision else
+                                    ("f64" if args.storage == "f64" else "f32"),
                        "stochastic_rounding": (args.sr if args.sr is not None else
                                                int(args.storage in ("f16", "bf16"))),
                        "l2": f"inputs larger than L2 ({lat_bytes(args.storage, N) / 1e9:.1f} GB "
