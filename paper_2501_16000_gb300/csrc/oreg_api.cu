@@ -482,10 +482,11 @@ olb_status olb_init_fields(olb_lattice *L, const double *rho, const double *ux, 
         s.rows = r;
         st = run_init(L, s);
         if (st != OLB_OK) return st;
-        // the scratch is reused by the next chunk and the host arrays may be
-        // reused on return
-        OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising field upload");
+        // the next chunk's copies into the scratch follow this chunk's kernel
+        // in stream order, so the host does not wait here
     }
+    // the host arrays may be reused on return
+    OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising field upload");
     return OLB_OK;
 }
 
@@ -561,8 +562,10 @@ olb_status olb_moments(olb_lattice *L, double *rho, double *ux, double *uy, doub
         if (theta_loc)
             OLB_CUDA(cudaMemcpyAsync(theta_loc + off, dt, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->stream),
                      "copying theta");
-        OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising moments");
+        // the next chunk's kernel overwrites the scratch after these copies in
+        // stream order, so the host does not wait here
     }
+    OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising moments");
     return OLB_OK;
 }
 
@@ -598,8 +601,9 @@ olb_status olb_get_populations(olb_lattice *L, double *f9) {
             OLB_CUDA(cudaMemcpyAsync(f9 + i * N + (size_t)y0 * nx, d + i * cnt, cnt * sizeof(double),
                                      cudaMemcpyDeviceToHost, L->stream),
                      "copying populations");
-        OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising population readback");
+        // scratch reuse by the next chunk is ordered by the stream
     }
+    OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising population readback");
     return OLB_OK;
 }
 
@@ -629,8 +633,9 @@ olb_status olb_get_region(olb_lattice *L, int32_t x0, int32_t y0, int32_t wx, in
             OLB_CUDA(cudaMemcpyAsync(f9 + i * W + (size_t)r0 * wx, d + i * cnt, cnt * sizeof(double),
                                      cudaMemcpyDeviceToHost, L->stream),
                      "copying region");
-        OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising region readback");
+        // scratch reuse by the next chunk is ordered by the stream
     }
+    OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising region readback");
     return OLB_OK;
 }
 
@@ -656,8 +661,9 @@ olb_status olb_set_populations(olb_lattice *L, const double *f9, int64_t t) {
                      "copying populations");
         OLB_CUDA(DISPATCH(L->p.storage, set_canonical, state_base(L), g, y0, r, L->kd, d, L->stream),
                  "launching population upload");
-        OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising population upload");
+        // scratch reuse by the next chunk is ordered by the stream
     }
+    OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising population upload");
     return OLB_OK;
 }
 
