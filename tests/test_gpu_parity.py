@@ -172,6 +172,27 @@ def test_fp64_collision_option_validation():
         assert e.value.status == B.OLB_ERR_INVALID
 
 
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+def test_block_size_does_not_change_results(storage, layout):
+    """OLB_OPT_WARPS_PER_BLOCK only changes how row segments map to blocks
+    (and, for the half formats, whether the register-capped A-B kernel runs):
+    results are bitwise the same for 1, 2, 4 and 8 warps per block."""
+    from paper_2501_16000_gb300 import binding as B
+    from paper_2501_16000_gb300.engine import Lattice
+    nx, ny = 131, 23
+    f0 = random_state(nx, ny, "guided", 1.0 / 3.0, seed=5)
+    got = {}
+    for w in (1, 2, 4, 8):
+        with Lattice(nx, ny, 0.7, storage=storage, layout=layout) as lat:
+            lat.set_option(B.OLB_OPT_WARPS_PER_BLOCK, w)
+            lat.set_populations(f0, 0)
+            lat.step(5)
+            got[w] = lat.populations()
+    for w in (1, 2, 8):
+        assert np.array_equal(got[w], got[4]), w
+
+
 def test_theta_off_reference_fp64():
     case = W.LatticeCase(nx=48, ny=40, tau=0.6, theta=0.3, case="shear", u0=0.05, m=2, n=1)
     err = rel_linf(gpu_run(case, 300, "f64", "aa"), oracle_run(case, 300))
