@@ -67,7 +67,8 @@ def test_required_bytes(lib, storage, layout, elem, nbuf):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(ny=-1), dict(tau=0.5), dict(tau=float("nan")), dict(rho0=0.0),
-    dict(theta=0.0), dict(theta=1.0), dict(eq="poly2", theta=0.3)])
+    dict(theta=0.0), dict(theta=1.0), dict(eq="poly2", theta=0.3),
+    dict(nx=1 << 20, ny=1 << 17)])   # 2^37 nodes: beyond the 2^36 limit (no size_t overflow)
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     p = _params(**bad)
     assert lib.olb_required_bytes(ctypes.byref(p)) == 0
