@@ -255,6 +255,26 @@ def test_half_precision_storage_short_runs(storage, bound, layout):
     assert err <= bound, err
 
 
+@pytest.mark.parametrize("storage,bound", [("f16", 2e-3), ("bf16", 1.6e-2)])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("nx,ny", SIZES)
+def test_half_precision_ragged_sizes(nx, ny, layout, storage, bound):
+    """The half formats on every ragged size (single nodes, single rows and
+    columns, partial vectors and segments) against the oracle, within the same
+    few-ulp bounds as the short-run test above, at even and odd times."""
+    from paper_2501_16000_gb300.engine import Lattice
+    f0 = random_state(nx, ny, "guided", 1.0 / 3.0, seed=nx * 7 + ny)
+    p = O.params(nx, ny, 0.7, 1.0 / 3.0, O.GUIDED, O.OREG)
+    with Lattice(nx, ny, 0.7, storage=storage, layout=layout) as lat:
+        lat.set_populations(f0, 0)
+        ref = f0
+        for steps in (1, 2):
+            lat.step(steps)
+            ref = O.run(ref, p, steps)
+            err = rel_linf(lat.populations(), ref)
+            assert err <= bound, (lat.time, err)
+
+
 # ---------------------------------------------------------------------------
 # state plumbing: round trips, checkpoint/resume, moments, diagnostics
 # ---------------------------------------------------------------------------
