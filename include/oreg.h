@@ -55,7 +55,8 @@ typedef enum { OLB_COLL_OREG = 0, OLB_COLL_BGK = 1 } olb_collision;
 /* Population storage.  Every format stores shifted values g_i = f_i - s_i,
  * with s_i the rest equilibrium w_i(theta) rho0 rounded to the compute type
  * (w = (1-theta)^2, theta(1-theta)/2, theta^2/4 for rest, axis and diagonal
- * directions).  F64 computes in double; F32, F16 and BF16 compute in float.
+ * directions).  F64 computes in double; F32, F16 and BF16 compute in float
+ * (F32 in double with OLB_OPT_F64_COLLISION).
  * F16 stores g * 2^8 (exact scaling) to keep small deviations out of the f16
  * subnormal range; |f_i - s_i| must stay below 255. */
 typedef enum {
