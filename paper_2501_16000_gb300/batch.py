@@ -23,17 +23,24 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 ITEM_ROW_GROUPS = 4
 
 
+def segment_lanes(nx: int, ny: int, v: int) -> int:
+    """Lanes W per row segment, as the library chooses them: a warp pass covers
+    32/W rows of one W-lane segment of W*v nodes, and W (a power of two <= 32)
+    needs the fewest passes; among equal counts the widest."""
+    best, best_passes = 32, None
+    for w in (32, 16, 8, 4, 2, 1):
+        passes = math.ceil(nx / (w * v)) * math.ceil(ny / (32 // w))
+        if best_passes is None or passes < best_passes:
+            best, best_passes = w, passes
+    return best
+
+
 def work_items(nx: int, ny: int, storage: str) -> int:
     """Warp work items of one lattice: a warp pass covers a row group of 32/W
-    rows of W-lane row segments, W the smallest power of two <= 32 whose W
-    16-byte vectors span the row; an item is up to ITEM_ROW_GROUPS row groups
-    of one segment."""
+    rows of one W-lane row segment (``segment_lanes``); an item is up to
+    ITEM_ROW_GROUPS row groups of one segment."""
     v = 16 // {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[storage]
-    vecs = math.ceil(nx / v)
-    lw = 0
-    while lw < 5 and (1 << lw) < vecs:
-        lw += 1
-    w = 1 << lw
+    w = segment_lanes(nx, ny, v)
     return math.ceil(math.ceil(ny / (32 // w)) / ITEM_ROW_GROUPS) * math.ceil(nx / (w * v))
 
 

@@ -501,7 +501,7 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     a.ny = L->p.ny;
     a.pitch = L->pitch;
     a.plane = L->plane;
-    a.lw = segment_log2(L->p.nx, L->V);
+    a.lw = segment_log2(L->p.nx, L->p.ny, L->V);
     a.segs = (L->p.nx + (L->V << a.lw) - 1) / (L->V << a.lw);
     a.eq = kernel_eq(&L->p);
     a.coll = L->p.coll;

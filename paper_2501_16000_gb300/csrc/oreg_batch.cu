@@ -74,7 +74,7 @@ void fill_desc(void *dst, const Member &m, const CollConst<C> &k) {
     d.pitch = L->pitch;
     d.eq = L->p.eq;
     d.coll = L->p.coll;
-    d.lw = segment_log2(L->p.nx, L->V);
+    d.lw = segment_log2(L->p.nx, L->p.ny, L->V);
     d.plane = L->plane;
     d.buf_elems = L->buf_elems;
     d.t_base = m.t_base;
@@ -124,7 +124,7 @@ olb_status upload(olb_batch *b) {
         else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf);
         const int cls = (int)((m.t_base - m.g_base) & 1);
         const int grp = combo_index(L) * 2 + cls;
-        const int lw = segment_log2(L->p.nx, L->V);
+        const int lw = segment_log2(L->p.nx, L->p.ny, L->V);
         const int segs = (L->p.nx + (L->V << lw) - 1) / (L->V << lw);
         const int rows = 32 >> lw;  // rows per row group (one warp pass)
         const int ngroups = (L->p.ny + rows - 1) / rows;

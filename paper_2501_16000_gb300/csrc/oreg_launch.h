@@ -39,13 +39,23 @@ struct StepArgs {
     cudaStream_t stream;
 };
 
-// Lanes per row segment for a lattice nx wide: the smallest power of two
-// W <= 32 whose segment (W vectors of V elements) covers the row, as log2.
-inline int segment_log2(int nx, int V) {
-    const int vecs = (nx + V - 1) / V;
-    int lw = 0;
-    while (lw < 5 && (1 << lw) < vecs) ++lw;
-    return lw;
+// Lanes per row segment for an nx x ny lattice, as log2: a warp pass covers
+// 32/W rows of one W-lane segment of W*V nodes, and W (a power of two <= 32)
+// is the one that needs the fewest passes, i.e. leaves the fewest lanes idle
+// on partial segments and partial row groups; among equal counts the widest
+// (fewest segment-edge halo loads).  Every W gives bitwise the same results.
+inline int segment_log2(int nx, int ny, int V) {
+    int best = 5;
+    long long best_passes = -1;
+    for (int lw = 5; lw >= 0; --lw) {
+        const long long seg = (long long)V << lw, rows = 32 >> lw;
+        const long long passes = ((nx + seg - 1) / seg) * ((ny + rows - 1) / rows);
+        if (best_passes < 0 || passes < best_passes) {
+            best = lw;
+            best_passes = passes;
+        }
+    }
+    return best;
 }
 
 enum { INIT_SHEAR = 0, INIT_SHOCK = 1, INIT_FIELDS = 2 };

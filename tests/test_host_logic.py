@@ -8,7 +8,7 @@ import pytest
 
 from paper_2501_16000_gb300 import workloads as W
 from paper_2501_16000_gb300.analysis import fit_decay
-from paper_2501_16000_gb300.batch import work_items
+from paper_2501_16000_gb300.batch import segment_lanes, work_items
 from paper_2501_16000_gb300.engine import required_bytes
 
 
@@ -56,15 +56,22 @@ def test_fit_decay_recovers_an_exponential():
 
 @pytest.mark.parametrize("storage,v", [("f64", 2), ("f32", 4), ("f16", 8)])
 def test_work_items_cover_every_node_once(storage, v):
-    for nx in (1, 5, 37, 100, 256, 257, 1024, 3000):
-        for ny in (1, 3, 32, 33):
-            vecs = math.ceil(nx / v)
-            w = 1
-            while w < 32 and w < vecs:
-                w *= 2
+    for nx in (1, 5, 33, 37, 100, 256, 257, 300, 1024, 3000, 8192):
+        for ny in (1, 3, 4, 32, 33, 500, 8192):
+            w = segment_lanes(nx, ny, v)
+            passes = {u: math.ceil(nx / (u * v)) * math.ceil(ny / (32 // u))
+                      for u in (1, 2, 4, 8, 16, 32)}
+            # fewest warp passes, the widest segment among equals
+            assert passes[w] == min(passes.values())
+            assert all(u <= w for u in passes if passes[u] == passes[w])
             groups = math.ceil(ny / (32 // w))
             assert work_items(nx, ny, storage) * 4 * 32 * v >= nx * ny
             assert work_items(nx, ny, storage) == math.ceil(groups / 4) * math.ceil(nx / (w * v))
+    # full-width segments where nothing idles (the benchmark lattice), narrower
+    # segments where a 32-lane one would leave lanes idle
+    assert segment_lanes(8192, 8192, v) == 32
+    assert segment_lanes(2048, 4, 4) == 32
+    assert segment_lanes(300, 500, 8) == 2 and segment_lanes(33, 500, 8) == 1
 
 
 class _FakeLattice:
