@@ -219,6 +219,14 @@ olb_status ensure_chunk(olb_lattice *L, size_t bytes) {
 }
 
 // rows per readback chunk for `per_node_doubles` FP64 values per node
+// Staged transfers queue their copies asynchronously and wait once at the
+// end; this guard also waits when a call returns early on an error, so that no
+// queued copy still reads or writes the caller's host arrays after the return.
+struct StreamDrain {
+    cudaStream_t s;
+    ~StreamDrain() { cudaStreamSynchronize(s); }
+};
+
 int chunk_rows(const olb_lattice *L, int per_node_doubles) {
     const size_t row_bytes = (size_t)L->p.nx * per_node_doubles * sizeof(double);
     size_t rows = CHUNK_BYTES_MAX / row_bytes;
@@ -467,6 +475,7 @@ olb_status olb_init_fields(olb_lattice *L, const double *rho, const double *ux, 
     st = ensure_chunk(L, (size_t)rows * nx * 3 * sizeof(double));
     if (st != OLB_OK) return st;
     double *d = static_cast<double *>(L->d_chunk);
+    StreamDrain drain_{L->stream};
     for (int y0 = 0; y0 < L->p.ny; y0 += rows) {
         const int r = std::min(rows, L->p.ny - y0);
         const size_t cnt = (size_t)r * nx, off = (size_t)y0 * nx;
@@ -547,6 +556,7 @@ olb_status olb_moments(olb_lattice *L, double *rho, double *ux, double *uy, doub
     st = ensure_chunk(L, (size_t)rows * nx * 4 * sizeof(double));
     if (st != OLB_OK) return st;
     double *d = static_cast<double *>(L->d_chunk);
+    StreamDrain drain_{L->stream};
     const StateGeom g = geom(L);
     for (int y0 = 0; y0 < L->p.ny; y0 += rows) {
         const int r = std::min(rows, L->p.ny - y0);
@@ -590,6 +600,7 @@ olb_status olb_get_populations(olb_lattice *L, double *f9) {
     st = ensure_chunk(L, (size_t)rows * nx * 9 * sizeof(double));
     if (st != OLB_OK) return st;
     double *d = static_cast<double *>(L->d_chunk);
+    StreamDrain drain_{L->stream};
     const StateGeom g = geom(L);
     for (int y0 = 0; y0 < L->p.ny; y0 += rows) {
         const int r = std::min(rows, L->p.ny - y0);
@@ -621,6 +632,7 @@ olb_status olb_get_region(olb_lattice *L, int32_t x0, int32_t y0, int32_t wx, in
     st = ensure_chunk(L, (size_t)rows * row_bytes);
     if (st != OLB_OK) return st;
     double *d = static_cast<double *>(L->d_chunk);
+    StreamDrain drain_{L->stream};
     const StateGeom g = geom(L);
     const size_t W = (size_t)wx * wy;
     for (int r0 = 0; r0 < wy; r0 += rows) {
@@ -651,6 +663,7 @@ olb_status olb_set_populations(olb_lattice *L, const double *f9, int64_t t) {
     if (st != OLB_OK) return st;
     L->t = t;
     double *d = static_cast<double *>(L->d_chunk);
+    StreamDrain drain_{L->stream};
     const StateGeom g = geom(L);
     for (int y0 = 0; y0 < L->p.ny; y0 += rows) {
         const int r = std::min(rows, L->p.ny - y0);
