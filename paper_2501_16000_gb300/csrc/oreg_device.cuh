@@ -141,15 +141,16 @@ template <> struct Storage<ST_BF16> {
     }
 };
 
-// Counter-based random bits for stochastic rounding: one hash per node pair
-// (x, x+1), x even, and time step (the 32-bit finalizer of MurmurHash3 of
-// (x/2, y, t)), then the nine directions' words as an arithmetic progression
-// r_i = h + i d (mod 2^32) with an odd step d mixed from h, one addition per
-// direction.  The low 16-bit half of r_i feeds node x, the high half node
-// x+1.  Each r_i is uniform when h is (so the rounding stays unbiased), and
-// for i != j the difference (i - j) d is itself random.  The draws depend
-// only on (x, y, t, i), so results do not depend on how nodes are scheduled,
-// batched or laid out.
+// Counter-based random bits for stochastic rounding: one hash per group of V
+// consecutive nodes (x0 = a multiple of V, the nodes of one lane) and time
+// step (the 32-bit finalizer of MurmurHash3 of (x0/V, y, t)), then the words
+// of its node pairs (x, x+1), x = x0 + 2p, and directions i as one arithmetic
+// progression r = h + (9p + i) d (mod 2^32) with an odd step d mixed from h,
+// one addition per word.  The low 16-bit half of a word feeds node x, the
+// high half node x+1.  Every word is uniform when h is (so the rounding stays
+// unbiased), and the difference of two words, a multiple of d, is itself
+// random.  The draws depend only on (x, y, t, i), so results do not depend
+// on how nodes are scheduled, batched or laid out.
 __device__ __forceinline__ uint32_t node_seed(int x, int y, long long t) {
     uint32_t h = (uint32_t)x * 0x9E3779B1u;
     h ^= (uint32_t)y * 0x85EBCA77u + 0x632BE5ABu;

@@ -85,8 +85,8 @@ __device__ __forceinline__ void zero_padding(typename Storage<S>::C f[9][Storage
 // or (half formats, sr) stochastically with counter-based bits per node,
 // time step and direction.
 // Half formats encode node pairs (x, x+1), x even, with one packed
-// conversion; the stochastic draws of a pair and direction i are
-// h + i pair_step(h), h = node_seed(x / 2, y, t).
+// conversion; the stochastic draw of pair p of the lane (x = xb + 2p) and
+// direction i is h + (9p + i) pair_step(h), h = node_seed(xb / V, y, t).
 template <int S>
 __device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Storage<S>::V],
                                            typename Storage<S>::T e[9][Storage<S>::V], int xb,
@@ -96,10 +96,10 @@ __device__ __forceinline__ void encode_vec(const typename Storage<S>::C f[9][Sto
     if constexpr (S == ST_F16 || S == ST_BF16) {
         uint32_t w[9][ST::V / 2];
         if (sr) {
+            const uint32_t h = node_seed(xb / ST::V, y, t), d = pair_step(h);
+            uint32_t r = h;
 #pragma unroll
             for (int j = 0; j < ST::V; j += 2) {
-                const uint32_t h = node_seed((xb + j) >> 1, y, t), d = pair_step(h);
-                uint32_t r = h;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     w[i][j / 2] = ST::enc2_stochastic(f[i][j], f[i][j + 1], r);
