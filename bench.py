@@ -56,7 +56,7 @@ def parse_args():
                     help="skip the batched, serving and precision sections")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=1000)
-    ap.add_argument("--decay-samples", type=int, default=12)
+    ap.add_argument("--decay-samples", type=int, default=60)
     ap.add_argument("--serve-count", type=int, default=300)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-side", type=int, default=1024)
