@@ -48,11 +48,12 @@ template <typename C> struct BatchDesc {
 // + coll) of BatchLaunch::combos).
 enum { BATCH_AB = 0, BATCH_AA_EVEN = 1, BATCH_AA_ODD = 2 };
 
-// At most 128 threads x 3 blocks per SM: the per-lattice constants come from
-// the descriptor in global memory rather than the parameter bank, and left to
-// itself the compiler keeps them all in registers (150-180 for half storage),
-// halving occupancy.  Measured on 512 mixed FP16 lattices: unbounded 78,
-// 128 registers (256 x 2) 88, 170 registers (128 x 3) 90 GLUPS.
+// At most 128 threads x 3 blocks per SM (a 170-register cap): the per-lattice
+// constants come from the descriptor in global memory rather than the
+// parameter bank, and left to itself the compiler keeps them all in registers
+// (150-180 for half storage), halving occupancy.  On 512 mixed FP16 lattices
+// tighter caps that buy more warps spill and run slower (128 registers: -10%,
+// 144: -4%; the kernel uses ~155 at this bound).
 constexpr int BATCH_MAX_THREADS = 128;
 template <int S, int KIND, int EQ, int COLL, bool WALLS>
 __global__ void __launch_bounds__(BATCH_MAX_THREADS, 3)
