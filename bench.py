@@ -200,9 +200,27 @@ def cpu_baseline(args, case, seconds: float):
         steps += 2
     dt = time.perf_counter() - t0
     mlups = side * side * steps / dt / 1e6
+    # the same oracle on one core, on a quarter-side sample for ~seconds / 3
+    side1 = max(64, side // 4)
+    m1, n1, _ = W.wave_vector_from_angle(side1, side1, math.atan2(case.n / case.ny, case.m / case.nx))
+    p1 = O.params(side1, side1, case.tau, case.theta, O.GUIDED, O.OREG)
+    f1 = O.init_equilibrium(p1, *W.shear_wave_fields(side1, side1, 1.0, case.u0, m1, n1))
+    O.set_threads(1)
+    try:
+        f1 = O.run(f1, p1, 1)
+        steps1, t1 = 0, time.perf_counter()
+        while time.perf_counter() - t1 < seconds / 3:
+            f1 = O.run(f1, p1, 2)
+            steps1 += 2
+        dt1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(threads)
     return {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
             "sample": f"{side}x{side} periodic shear wave, same tau/theta/u0, {steps} FP64 "
-                      f"steps in {dt:.1f} s, OpenMP over rows ({threads} threads)"}
+                      f"steps in {dt:.1f} s, OpenMP over rows ({threads} threads)",
+            "single_thread": {"value": round(side1 * side1 * steps1 / dt1 / 1e6, 3),
+                              "unit": "MLUPS", "cores": 1,
+                              "sample": f"{side1}x{side1}, {steps1} FP64 steps in {dt1:.1f} s"}}
 
 
 def run_reference(args):
