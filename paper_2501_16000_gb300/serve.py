@@ -6,9 +6,12 @@ as soon as their population memory (``olb_required_bytes``) fits the HBM
 budget next to everything in flight; admitted requests join the running
 ``BatchEngine`` and advance together with all other in-flight requests, one
 CUDA-graph round of K steps at a time, their states resident in HBM.  A
-request whose steps are done is read back (moments to host), removed and its
-memory freed, which may admit the next ones.  Latency is arrival -> result in
-host memory.
+request whose steps are done is checked (FP64 diagnostics: a solve that turned
+non-finite is reported with status "nonfinite" and no fields), read back
+(moments to host), removed and its memory freed, which may admit the next
+ones.  A request can be cancelled while it waits or while it runs (status
+"cancelled"; an in-flight one leaves the batch at the next round boundary and
+frees its memory).  Latency is arrival -> result in host memory.
 
 ``serve_serial`` replays the same trace with one plain FP32 single-lattice
 solve at a time (the baseline).
@@ -35,6 +38,7 @@ class Result:
     steps: int
     case: str
     fields: tuple | None = None
+    status: str = "ok"          # "ok", "nonfinite" or "cancelled"
 
     @property
     def latency_s(self) -> float:
@@ -42,11 +46,18 @@ class Result:
 
 
 def summarize(results, wall_s, label):
+    """Throughput and latency of the completed ("ok") solves; failed and
+    cancelled requests are counted separately."""
+    failed = sum(r.status == "nonfinite" for r in results)
+    cancelled = sum(r.status == "cancelled" for r in results)
+    results = [r for r in results if r.status == "ok"]
     lat = np.array([r.latency_s for r in results])
     work = sum(r.nodes * r.steps for r in results)
     return {
         "label": label,
         "solves": len(results),
+        "nonfinite": failed,
+        "cancelled": cancelled,
         "wall_s": round(wall_s, 3),
         "solves_per_s": round(len(results) / wall_s, 2) if wall_s > 0 else None,
         "mlups": round(work / wall_s / 1e6, 1) if wall_s > 0 else None,
@@ -83,9 +94,14 @@ class Server:
     def close(self):
         self.engine.close()
 
-    def run(self, trace, time_scale: float = 1.0):
+    def run(self, trace, time_scale: float = 1.0, cancel_at=None, prepare=None):
         """Serves the trace in real time (arrival times scaled by time_scale);
-        returns (results, wall seconds)."""
+        returns (results, wall seconds).
+
+        cancel_at: {rid: trace time} at which a request is cancelled (a
+        waiting one is dropped, an in-flight one removed from the batch).
+        prepare(request, lattice): called once a request's lattice is created
+        and initialised, before it joins the batch."""
         eng = self.engine
         pending = collections.deque(sorted(trace, key=lambda r: r.arrival_s))
         queue = collections.deque()
@@ -93,12 +109,34 @@ class Server:
         in_bytes = 0
         in_items = 0
         results = []
+        cancels = dict(cancel_at or {})
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
+
+        def cancelled(req, admitted_s):
+            return Result(req.rid, req.arrival_s * time_scale, admitted_s, now(),
+                          req.lattice.nodes, req.lattice.steps, req.lattice.case, None,
+                          "cancelled")
+
         while pending or queue or inflight:
             t = now()
             while pending and pending[0].arrival_s * time_scale <= t:
                 queue.append(pending.popleft())
+            # cancellations that are due: drop waiting requests, evict running ones
+            for rid in [r for r, ct in cancels.items() if ct * time_scale <= t]:
+                del cancels[rid]
+                for dq in (pending, queue):
+                    hit = [q for q in dq if q.rid == rid]
+                    for q in hit:
+                        dq.remove(q)
+                        results.append(cancelled(q, now()))
+                if rid in inflight:
+                    req, lat, need, adm = inflight.pop(rid)
+                    eng.remove(lat)
+                    lat.close()
+                    in_bytes -= need
+                    in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage)
+                    results.append(cancelled(req, adm))
             # FIFO admission against the memory budget (and the item table)
             while queue:
                 req = queue[0]
@@ -110,6 +148,8 @@ class Server:
                     break
                 queue.popleft()
                 lat = eng.new_lattice(req.lattice)
+                if prepare is not None:
+                    prepare(req, lat)
                 eng.add(lat, req.lattice.steps)
                 inflight[req.rid] = (req, lat, need, now())
                 in_bytes += need
@@ -127,14 +167,15 @@ class Server:
             self.rounds += 1
             for rid in [r for r, (_, lat, _, _) in inflight.items() if eng.remaining(lat) == 0]:
                 req, lat, need, adm = inflight.pop(rid)
-                fields = lat.moments() if self.keep_fields else None
+                ok = lat.diagnostics(raise_nonfinite=False)["nonfinite"] == 0
+                fields = lat.moments() if self.keep_fields and ok else None
                 eng.remove(lat)
                 lat.close()
                 in_bytes -= need
                 in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage)
                 results.append(Result(rid, req.arrival_s * time_scale, adm, now(),
                                       req.lattice.nodes, req.lattice.steps, req.lattice.case,
-                                      fields))
+                                      fields, "ok" if ok else "nonfinite"))
         return results, now()
 
 

@@ -57,3 +57,40 @@ def test_admission_respects_the_budget():
     srv.close()
     assert len(results) == len(trace)
     assert srv.peak_bytes <= budget
+
+
+def test_nonfinite_request_is_reported_and_the_others_are_unaffected():
+    """A NaN planted on the host in one request's populations (before it joins
+    the batch) makes that request come back with status "nonfinite" and no
+    fields; a request cancelled before it arrives is never admitted; every
+    other result stays bitwise equal to the same request solved alone."""
+    from paper_2501_16000_gb300.engine import Lattice
+    from paper_2501_16000_gb300.serve import Server
+    trace = small_trace(n=10, seed=5)
+    by_arrival = sorted(trace, key=lambda r: r.arrival_s)
+    poison, early = by_arrival[1].rid, by_arrival[-1].rid
+
+    def prepare(req, lat):
+        if req.rid == poison:
+            f = lat.populations()
+            f[2, lat.ny // 2, lat.nx // 2] = np.nan
+            lat.set_populations(f, 0)
+
+    srv = Server("f16", "ab", budget_bytes=1e9, steps_per_launch=16)
+    results, _ = srv.run(trace, cancel_at={early: -1.0}, prepare=prepare)
+    srv.close()
+    by_id = {r.rid: r for r in results}
+    assert sorted(by_id) == sorted(r.rid for r in trace)
+    assert by_id[poison].status == "nonfinite" and by_id[poison].fields is None
+    assert by_id[early].status == "cancelled"
+    for req in trace:
+        if req.rid in (poison, early):
+            continue
+        c = req.lattice
+        with Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, "f16", "ab") as lat:
+            lat.init_case(c)
+            lat.step(c.steps)
+            alone = lat.moments()
+        assert by_id[req.rid].status == "ok"
+        for a, b in zip(alone, by_id[req.rid].fields):
+            assert np.array_equal(a, b), req.rid

@@ -2,6 +2,7 @@
 work-item count and the serving loop's admission against a memory budget
 (with a stand-in for the GPU batch engine)."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -76,10 +77,13 @@ def test_work_items_cover_every_node_once(storage, v):
 
 class _FakeLattice:
     def __init__(self, case):
-        self.case, self.closed = case, False
+        self.case, self.closed, self.poisoned = case, False, False
 
     def moments(self):
         return (np.ones((self.case.ny, self.case.nx)),) * 3
+
+    def diagnostics(self, raise_nonfinite=True):
+        return {"mass": 1.0, "mom_x": 0.0, "mom_y": 0.0, "nonfinite": 7 if self.poisoned else 0}
 
     def close(self):
         self.closed = True
@@ -88,8 +92,9 @@ class _FakeLattice:
 class _FakeEngine:
     """Advances every member K steps per round; no GPU."""
 
-    def __init__(self, K):
+    def __init__(self, K, round_s=0.0):
         self.K, self.left, self.order, self.rounds = K, {}, [], 0
+        self.round_s, self.evicted = round_s, []
 
     def new_lattice(self, case):
         return _FakeLattice(case)
@@ -99,6 +104,8 @@ class _FakeEngine:
         self.order.append(lat.case)
 
     def remove(self, lat):
+        if self.left[id(lat)] > 0:
+            self.evicted.append(lat.case)
         del self.left[id(lat)]
 
     def remaining(self, lat):
@@ -106,6 +113,8 @@ class _FakeEngine:
 
     def run(self, n=1):
         self.rounds += n
+        if self.round_s:
+            time.sleep(self.round_s * n)
         for k in self.left:
             self.left[k] = max(0, self.left[k] - n * self.K)
 
@@ -176,3 +185,39 @@ def test_paper_workloads_use_the_printed_parameters():
     assert c.nx == round(d["grid"][1] * math.sqrt(2))
     assert np.allclose(ux, s, rtol=0, atol=1e-15)
     assert np.allclose(uy, c.uy_mean + s, rtol=0, atol=1e-15)
+
+
+def test_serving_reports_nonfinite_and_cancelled_requests():
+    """A request whose solve turns non-finite is reported as such, without
+    fields; cancelled requests are dropped while waiting or evicted while
+    running, their memory freed; every other request completes."""
+    from paper_2501_16000_gb300 import build
+    build.build()
+    from paper_2501_16000_gb300.serve import Server, summarize
+    trace = W.arrival_trace(24, rate_per_s=500.0, seed=9, lo=16, hi=128, steps_lo=100,
+                            steps_hi=2000)
+    by_arrival = sorted(trace, key=lambda r: r.arrival_s)
+    long_run = max(trace, key=lambda r: r.lattice.steps)      # cancelled while running
+    early = next(r.rid for r in reversed(by_arrival) if r.rid != long_run.rid)  # before arrival
+    poison = next(r.rid for r in by_arrival if r.rid not in (long_run.rid, early))
+    sizes = [required_bytes(nx=r.lattice.nx, ny=r.lattice.ny, tau=r.lattice.tau,
+                            storage="f16", layout="ab") for r in trace]
+    eng = _FakeEngine(K=50, round_s=0.002)
+    srv = Server("f16", "ab", budget_bytes=sum(sizes), engine=eng)
+    cancel_at = {early: -1.0, long_run.rid: long_run.arrival_s + 0.006}
+    results, wall = srv.run(trace, cancel_at=cancel_at,
+                            prepare=lambda req, lat: setattr(lat, "poisoned", req.rid == poison))
+    status = {r.rid: r.status for r in results}
+    assert sorted(status) == sorted(r.rid for r in trace)       # every request answered once
+    assert status[poison] == "nonfinite"
+    assert next(r for r in results if r.rid == poison).fields is None
+    assert status[early] == "cancelled" and early not in [c for c in eng.order]
+    assert status[long_run.rid] == "cancelled"
+    assert long_run.lattice in eng.evicted                    # it was running
+    for r in results:
+        if r.rid not in cancel_at and r.rid != poison:
+            assert r.status == "ok" and r.fields is not None
+    s = summarize(results, wall, "fake")
+    assert s["nonfinite"] == 1 and s["cancelled"] == len(cancel_at)
+    assert s["solves"] == len(trace) - 1 - len(cancel_at)
+    assert not eng.left                                        # nothing left in the batch
