@@ -228,13 +228,13 @@ struct F2 {
     __device__ __forceinline__ explicit F2(int a) : F2((float)a) {}
     __device__ __forceinline__ explicit F2(double a) : F2((float)a) {}
     __device__ __forceinline__ float lo() const {
-        float a, b;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+        float a;
+        asm("mov.b64 {%0, _}, %1;" : "=f"(a) : "l"(v));
         return a;
     }
     __device__ __forceinline__ float hi() const {
-        float a, b;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+        float b;
+        asm("mov.b64 {_, %0}, %1;" : "=f"(b) : "l"(v));
         return b;
     }
 };

@@ -274,18 +274,22 @@ __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict
     }
 }
 
+// One warp per work item (a row group of one segment); the grid covers them all.
+#define OREG_AB_BODY                                                                        \
+    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  \
+    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);                                   \
+    if (item >= (long long)groups * segs) return; /* warp-uniform */                        \
+    item_ab<S, EQ, COLL, COMP, WALLS>(src, dst, nx, ny, pitch, plane,                        \
+                                      (int)(item / segs) << (5 - lw), (int)(item % segs),   \
+                                      threadIdx.x & 31, lw, k, t, sr);
+
 template <int S, int EQ, int COLL, bool COMP, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *__restrict__ src,
                                                  typename Storage<S>::T *__restrict__ dst, int nx,
                                                  int ny, int pitch, size_t plane, int segs,
                                                  int lw, const CollConst<typename Storage<S>::C> k,
                                                  long long t, bool sr) {
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
-    if (item >= (long long)groups * segs) return;  // warp-uniform
-    item_ab<S, EQ, COLL, COMP, WALLS>(src, dst, nx, ny, pitch, plane,
-                                      (int)(item / segs) << (5 - lw), (int)(item % segs),
-                                      threadIdx.x & 31, lw, k, t, sr);
+    OREG_AB_BODY
 }
 
 // The same A-B step for the issue-bound half formats, periodic and at a fixed
@@ -303,13 +307,9 @@ __global__ void __launch_bounds__(AB_CAPPED_MAX_THREADS, 5)
                      typename Storage<S>::T *__restrict__ dst, int nx, int ny, int pitch,
                      size_t plane, int segs, int lw, const CollConst<typename Storage<S>::C> k,
                      long long t, bool sr) {
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
-    if (item >= (long long)groups * segs) return;  // warp-uniform
-    item_ab<S, EQ, COLL, COMP, WALLS>(src, dst, nx, ny, pitch, plane,
-                                      (int)(item / segs) << (5 - lw), (int)(item % segs),
-                                      threadIdx.x & 31, lw, k, t, sr);
+    OREG_AB_BODY
 }
+#undef OREG_AB_BODY
 
 // ---------------------------------------------------------------------------
 // Stream-collide, in-place AA layout.
