@@ -209,6 +209,7 @@ olb_status ensure_chunk(olb_lattice *L, size_t bytes) {
     if (L->chunk_bytes >= bytes) return OLB_OK;
     if (L->d_chunk) {
         cudaStreamSynchronize(L->stream);
+        if (L->copy_stream) cudaStreamSynchronize(L->copy_stream);
         cudaFree(L->d_chunk);
         L->d_chunk = nullptr;
         L->chunk_bytes = 0;
@@ -218,15 +219,29 @@ olb_status ensure_chunk(olb_lattice *L, size_t bytes) {
     return OLB_OK;
 }
 
-// rows per readback chunk for `per_node_doubles` FP64 values per node
 // Staged transfers queue their copies asynchronously and wait once at the
 // end; this guard also waits when a call returns early on an error, so that no
 // queued copy still reads or writes the caller's host arrays after the return.
 struct StreamDrain {
     cudaStream_t s;
-    ~StreamDrain() { cudaStreamSynchronize(s); }
+    ~StreamDrain() {
+        if (s) cudaStreamSynchronize(s);
+    }
 };
 
+// The copy stream and events of the double-buffered field upload and moments
+// readback (created on first use, released by olb_destroy).
+olb_status ensure_pipeline(olb_lattice *L) {
+    if (L->copy_stream) return OLB_OK;
+    OLB_CUDA(cudaStreamCreateWithFlags(&L->copy_stream, cudaStreamNonBlocking), "creating copy stream");
+    for (int b = 0; b < 2; ++b) {
+        OLB_CUDA(cudaEventCreateWithFlags(&L->ev_main[b], cudaEventDisableTiming), "creating event");
+        OLB_CUDA(cudaEventCreateWithFlags(&L->ev_copy[b], cudaEventDisableTiming), "creating event");
+    }
+    return OLB_OK;
+}
+
+// rows per readback chunk for `per_node_doubles` FP64 values per node
 int chunk_rows(const olb_lattice *L, int per_node_doubles) {
     const size_t row_bytes = (size_t)L->p.nx * per_node_doubles * sizeof(double);
     size_t rows = CHUNK_BYTES_MAX / row_bytes;
@@ -469,19 +484,31 @@ olb_status olb_init_fields(olb_lattice *L, const double *rho, const double *ux, 
     olb_status st = check_lattice(L, false);
     if (st != OLB_OK) return st;
     if (!rho || !ux || !uy) return fail(OLB_ERR_INVALID, "field arrays must not be NULL");
-    // fields are staged through the bounded readback scratch, a chunk of rows at a time
+    // fields are staged through the bounded readback scratch, a chunk of rows
+    // at a time, alternating between its two halves: the copies of chunk k
+    // (copy stream) overlap the conversion kernel of chunk k-1 (lattice stream)
     const int rows = chunk_rows(L, 3);
-    const size_t nx = L->p.nx;
-    st = ensure_chunk(L, (size_t)rows * nx * 3 * sizeof(double));
+    const size_t nx = L->p.nx, half = (size_t)rows * nx * 3;
+    st = ensure_chunk(L, 2 * half * sizeof(double));
     if (st != OLB_OK) return st;
-    double *d = static_cast<double *>(L->d_chunk);
-    StreamDrain drain_{L->stream};
-    for (int y0 = 0; y0 < L->p.ny; y0 += rows) {
+    st = ensure_pipeline(L);
+    if (st != OLB_OK) return st;
+    double *base = static_cast<double *>(L->d_chunk);
+    StreamDrain drain_{L->stream}, drain_copy_{L->copy_stream};
+    // copies into either half wait for the lattice stream's earlier work
+    for (int b = 0; b < 2; ++b)
+        OLB_CUDA(cudaEventRecord(L->ev_main[b], L->stream), "recording event");
+    for (int y0 = 0, k = 0; y0 < L->p.ny; y0 += rows, ++k) {
+        const int b = k & 1;
+        double *d = base + b * half;
         const int r = std::min(rows, L->p.ny - y0);
         const size_t cnt = (size_t)r * nx, off = (size_t)y0 * nx;
-        OLB_CUDA(cudaMemcpyAsync(d, rho + off, cnt * sizeof(double), cudaMemcpyHostToDevice, L->stream), "copying rho");
-        OLB_CUDA(cudaMemcpyAsync(d + cnt, ux + off, cnt * sizeof(double), cudaMemcpyHostToDevice, L->stream), "copying ux");
-        OLB_CUDA(cudaMemcpyAsync(d + 2 * cnt, uy + off, cnt * sizeof(double), cudaMemcpyHostToDevice, L->stream), "copying uy");
+        OLB_CUDA(cudaStreamWaitEvent(L->copy_stream, L->ev_main[b], 0), "ordering copy");
+        OLB_CUDA(cudaMemcpyAsync(d, rho + off, cnt * sizeof(double), cudaMemcpyHostToDevice, L->copy_stream), "copying rho");
+        OLB_CUDA(cudaMemcpyAsync(d + cnt, ux + off, cnt * sizeof(double), cudaMemcpyHostToDevice, L->copy_stream), "copying ux");
+        OLB_CUDA(cudaMemcpyAsync(d + 2 * cnt, uy + off, cnt * sizeof(double), cudaMemcpyHostToDevice, L->copy_stream), "copying uy");
+        OLB_CUDA(cudaEventRecord(L->ev_copy[b], L->copy_stream), "recording event");
+        OLB_CUDA(cudaStreamWaitEvent(L->stream, L->ev_copy[b], 0), "ordering conversion");
         InitSpec s{};
         s.mode = INIT_FIELDS;
         s.rho = d;
@@ -491,10 +518,10 @@ olb_status olb_init_fields(olb_lattice *L, const double *rho, const double *ux, 
         s.rows = r;
         st = run_init(L, s);
         if (st != OLB_OK) return st;
-        // the next chunk's copies into the scratch follow this chunk's kernel
-        // in stream order, so the host does not wait here
+        OLB_CUDA(cudaEventRecord(L->ev_main[b], L->stream), "recording event");
     }
-    // the host arrays may be reused on return
+    // the host arrays may be reused on return (every copy precedes a kernel
+    // of the lattice stream)
     OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising field upload");
     return OLB_OK;
 }
@@ -551,31 +578,46 @@ olb_status olb_moments(olb_lattice *L, double *rho, double *ux, double *uy, doub
     olb_status st = check_lattice(L, true);
     if (st != OLB_OK) return st;
     if (!rho || !ux || !uy) return fail(OLB_ERR_INVALID, "rho, ux, uy must not be NULL");
+    // chunks alternate between the two halves of the scratch: the kernel of
+    // chunk k (lattice stream) overlaps the copies of chunk k-1 (copy stream)
     const int rows = chunk_rows(L, 4);
-    const size_t nx = L->p.nx;
-    st = ensure_chunk(L, (size_t)rows * nx * 4 * sizeof(double));
+    const size_t nx = L->p.nx, half = (size_t)rows * nx * 4;
+    st = ensure_chunk(L, 2 * half * sizeof(double));
     if (st != OLB_OK) return st;
-    double *d = static_cast<double *>(L->d_chunk);
-    StreamDrain drain_{L->stream};
+    st = ensure_pipeline(L);
+    if (st != OLB_OK) return st;
+    double *base = static_cast<double *>(L->d_chunk);
+    StreamDrain drain_{L->stream}, drain_copy_{L->copy_stream};
+    // kernels may write either half once the copy stream's earlier copies are done
+    for (int b = 0; b < 2; ++b)
+        OLB_CUDA(cudaEventRecord(L->ev_copy[b], L->copy_stream), "recording event");
     const StateGeom g = geom(L);
-    for (int y0 = 0; y0 < L->p.ny; y0 += rows) {
+    for (int y0 = 0, k = 0; y0 < L->p.ny; y0 += rows, ++k) {
+        const int b = k & 1;
+        double *d = base + b * half;
         const int r = std::min(rows, L->p.ny - y0);
         const size_t cnt = (size_t)r * nx;
         double *dr = d, *dx = d + cnt, *dy = d + 2 * cnt, *dt = theta_loc ? d + 3 * cnt : nullptr;
+        OLB_CUDA(cudaStreamWaitEvent(L->stream, L->ev_copy[b], 0), "ordering kernel");
         OLB_CUDA(DISPATCH(L->p.storage, moments, state_base(L), g, y0, r, L->kd, dr, dx, dy, dt,
                           L->stream),
                  "launching moments kernel");
+        OLB_CUDA(cudaEventRecord(L->ev_main[b], L->stream), "recording event");
+        OLB_CUDA(cudaStreamWaitEvent(L->copy_stream, L->ev_main[b], 0), "ordering copy");
         const size_t off = (size_t)y0 * nx;
-        OLB_CUDA(cudaMemcpyAsync(rho + off, dr, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->stream), "copying rho");
-        OLB_CUDA(cudaMemcpyAsync(ux + off, dx, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->stream), "copying ux");
-        OLB_CUDA(cudaMemcpyAsync(uy + off, dy, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->stream), "copying uy");
+        OLB_CUDA(cudaMemcpyAsync(rho + off, dr, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->copy_stream), "copying rho");
+        OLB_CUDA(cudaMemcpyAsync(ux + off, dx, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->copy_stream), "copying ux");
+        OLB_CUDA(cudaMemcpyAsync(uy + off, dy, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->copy_stream), "copying uy");
         if (theta_loc)
-            OLB_CUDA(cudaMemcpyAsync(theta_loc + off, dt, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->stream),
+            OLB_CUDA(cudaMemcpyAsync(theta_loc + off, dt, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->copy_stream),
                      "copying theta");
-        // the next chunk's kernel overwrites the scratch after these copies in
-        // stream order, so the host does not wait here
+        OLB_CUDA(cudaEventRecord(L->ev_copy[b], L->copy_stream), "recording event");
     }
-    OLB_CUDA(cudaStreamSynchronize(L->stream), "synchronising moments");
+    // the scratch is reused by later calls on the lattice stream: order it
+    // after these copies; the host arrays are complete once the copy stream is
+    OLB_CUDA(cudaStreamWaitEvent(L->stream, L->ev_copy[0], 0), "ordering scratch reuse");
+    OLB_CUDA(cudaStreamWaitEvent(L->stream, L->ev_copy[1], 0), "ordering scratch reuse");
+    OLB_CUDA(cudaStreamSynchronize(L->copy_stream), "synchronising moments");
     return OLB_OK;
 }
 
@@ -742,6 +784,14 @@ olb_status olb_destroy(olb_lattice *L) {
     if (L->own_mem && L->mem) cudaFree(L->mem);
     if (L->d_red) cudaFree(L->d_red);
     if (L->h_red) cudaFreeHost(L->h_red);
+    if (L->copy_stream) {
+        cudaStreamSynchronize(L->copy_stream);
+        for (int b = 0; b < 2; ++b) {
+            cudaEventDestroy(L->ev_main[b]);
+            cudaEventDestroy(L->ev_copy[b]);
+        }
+        cudaStreamDestroy(L->copy_stream);
+    }
     if (L->d_chunk) cudaFree(L->d_chunk);
     if (L->d_tab) cudaFree(L->d_tab);
     if (L->h_tab) cudaFreeHost(L->h_tab);

@@ -35,6 +35,12 @@ struct olb_lattice {
     int red_blocks;
     void *d_chunk;        // readback scratch (lazy)
     size_t chunk_bytes;
+    // Field upload and moments readback alternate between two halves of the
+    // scratch and run their copies on copy_stream, so that the copies of one
+    // chunk overlap the conversion kernel of the other (lazy).
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_main[2];  // recorded on the lattice's stream, per half
+    cudaEvent_t ev_copy[2];  // recorded on copy_stream, per half
     double *d_tab;        // shear-mode sin/cos tables (lazy), for (tab_m, tab_n)
     double *h_tab;
     int tab_m, tab_n;
