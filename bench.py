@@ -45,7 +45,8 @@ def parse_args():
     ap.add_argument("--theta", type=float, default=1.0 / 3.0)
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--layout", default="ab", choices=["ab", "aa"])
-    ap.add_argument("--comp", type=int, default=0, help="OLB_OPT_COMPENSATED (FP32)")
+    ap.add_argument("--comp", type=int, default=None,
+                    help="OLB_OPT_COMPENSATED for f32: exact conserved sums (library default: 1)")
     ap.add_argument("--warps", type=int, default=4, help="OLB_OPT_WARPS_PER_BLOCK")
     ap.add_argument("--sr", type=int, default=None,
                     help="OLB_OPT_STOCHASTIC_ROUNDING for f16/bf16 (library default: 1)")
@@ -292,7 +293,8 @@ def run_native(args):
     stream = torch.cuda.Stream()
     lat = Lattice(case.nx, case.ny, case.tau, case.theta, "guided", "oreg", args.storage,
                   args.layout, stream=stream)
-    lat.set_option(B.OLB_OPT_COMPENSATED, args.comp)
+    if args.comp is not None:
+        lat.set_option(B.OLB_OPT_COMPENSATED, args.comp)
     lat.set_option(B.OLB_OPT_WARPS_PER_BLOCK, args.warps)
     if args.sr is not None:
         lat.set_option(B.OLB_OPT_STOCHASTIC_ROUNDING, args.sr)
@@ -397,7 +399,9 @@ def run_native(args):
                        "nodes": N, "theta": case.theta, "tau": case.tau, "u0": case.u0,
                        "wave": [case.m, case.n], "storage": args.storage,
                        "layout": args.layout, "diagnostics_every": DIAG_EVERY,
-                       "compensated": args.comp, "warps_per_block": args.warps,
+                       "exact_conserved_sums": (args.comp if args.comp is not None else
+                                                int(args.storage == "f32")),
+                       "warps_per_block": args.warps,
                        "collision": "f64" if args.f64_collision else
                                     ("f64" if args.storage == "f64" else "f32"),
                        "stochastic_rounding": (args.sr if args.sr is not None else

@@ -114,11 +114,16 @@ typedef struct {
 
 /* Tuning and precision options of a lattice (olb_set_option). */
 typedef enum {
-    /* 1: accumulate the conserved moments (mass, momentum) of the FP32
-       collision with error-free (TwoSum) additions, which keeps their FP32
-       rounding out of long runs (about half the drift from FP64 on a
-       weakly damped shock tube) at ~13% of the FP32 kernel's throughput;
-       0 (default): plain sums.  Ignored by the other formats. */
+    /* OLB_F32 storage.  1 (default): the conserved moments (mass and
+       momentum) of the FP32 collision are exact sums of the stored
+       populations, rounded once (an error-free split of each population
+       against a power-of-two constant; about 50 more FP32 additions per
+       node).  Plain FP32 sums round each partial sum, and the rounding
+       repeats identically at every node of a uniform region and every
+       step: on the 2048 x 4 shock tube (tau = 0.51, 2000 steps) they end
+       ~3e-5 from the FP64 scheme, the exact sums ~5e-6.  0: plain sums
+       (olb_batch_add rejects an FP32 lattice with 0).  Ignored by the other
+       formats. */
     OLB_OPT_COMPENSATED = 1,
     /* warps per thread block of the stream-collide kernels: 1, 2, 4 or 8
        (default 4).  A warp updates 32/W row segments of W*V consecutive
@@ -135,12 +140,11 @@ typedef enum {
     OLB_OPT_STOCHASTIC_ROUNDING = 3,
     /* OLB_F32 storage only.  1: olb_step computes the collision in FP64
        (decode, Eqs. 6-7, encode) while the populations stay stored in
-       FP32, so the store is the only FP32 rounding of a step.  Over long,
-       weakly damped runs the FP32 collision's own rounding dominates the
-       drift from the FP64 result (2048 x 4 shock tube, tau = 0.51, 2000
-       steps: ~2e-5 relative with the FP32 collision, ~4e-6 from the FP32
-       store alone); this mode is for such accuracy runs, at the GPU's FP64
-       rate (a few GLUPS).  The stored state is that of the FP32 collision
+       FP32, so the store is the only FP32 rounding of a step (2048 x 4
+       shock tube, tau = 0.51, 2000 steps: ~5e-6 from the FP64 result,
+       like the default FP32 collision with exact conserved sums); a
+       reference mode for accuracy studies, at the GPU's FP64 rate (a few
+       GLUPS).  The stored state is that of the FP32 collision
        (same elements and shifts), so the option may change between steps.
        0 (default): FP32 collision.  OLB_ERR_INVALID for value 1 on another
        storage format; olb_batch_add rejects a lattice with it set. */

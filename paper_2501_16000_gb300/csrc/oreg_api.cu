@@ -141,6 +141,8 @@ CollConst<C> make_const(const olb_params *p) {
     }
     k.sum_corr = (C)corr_sum;
     k.rho0 = (C)p->rho0;
+    // split constant of the exact conserved sums: 1.5 * 2^e, 2^e >= 32 rho0
+    k.sigma = (C)(1.5 * std::exp2(std::ceil(std::log2(32.0 * p->rho0))));
     k.lam = (C)(1.0 - 1.0 / p->tau);
     k.inv_2th2 = (C)(1.0 / (2.0 * th * th));
     k.theta = (C)th;
@@ -349,7 +351,7 @@ olb_status olb_create_lattice(const olb_params *p, olb_lattice **out) {
     L->buf_elems = 9 * L->plane;
     L->nbuf = p->layout == OLB_LAYOUT_AB ? 2 : 1;
     L->t = -1;
-    L->comp = 0;
+    L->comp = p->storage == OLB_F32 ? 1 : 0;
     L->f64_coll = 0;
     L->sr = (p->storage == OLB_F16_SHIFTED || p->storage == OLB_BF16_SHIFTED) ? 1 : 0;
     L->warps_per_block = 4;

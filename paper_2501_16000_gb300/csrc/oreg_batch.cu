@@ -269,6 +269,9 @@ olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps) {
     if (lat->t < 0) return bfail(OLB_ERR_STATE, "lattice state not initialised");
     if (lat->f64_coll)
         return bfail(OLB_ERR_INVALID, "OLB_OPT_F64_COLLISION is not available in a batch");
+    if (lat->p.storage == OLB_F32 && !lat->comp)
+        return bfail(OLB_ERR_INVALID, "batches use the exact conserved sums of FP32 storage: "
+                                      "OLB_OPT_COMPENSATED = 0 is not available in a batch");
     if (lat->p.storage != b->p.storage || lat->p.layout != b->p.layout)
         return bfail(OLB_ERR_INVALID, "lattice storage/layout (%d/%d) differ from the batch's (%d/%d)",
                      lat->p.storage, lat->p.layout, b->p.storage, b->p.layout);

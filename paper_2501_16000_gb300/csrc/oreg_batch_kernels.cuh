@@ -87,13 +87,13 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 3)
             if constexpr (KIND == BATCH_AB) {
                 const T *src = base + (size_t)(t & 1) * d.buf_elems;
                 T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
-                item_ab<S, EQ, COLL, false, WALLS>(src, dst, d.nx, d.ny, d.pitch, d.plane, y0,
+                item_ab<S, EQ, COLL, S == ST_F32, WALLS>(src, dst, d.nx, d.ny, d.pitch, d.plane, y0,
                                                    it.z, lane, d.lw, d.k, t, d.sr != 0);
             } else if constexpr (KIND == BATCH_AA_ODD) {
-                item_aa_odd<S, EQ, COLL, false, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
+                item_aa_odd<S, EQ, COLL, S == ST_F32, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
                                                        it.z, lane, d.lw, d.k, t, d.sr != 0);
             } else {
-                item_aa_even<S, EQ, COLL, false, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
+                item_aa_even<S, EQ, COLL, S == ST_F32, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
                                                         it.z, lane, d.lw, d.k, t, d.sr != 0);
             }
         }

@@ -204,6 +204,8 @@ template <typename C> struct CollConst {
     C shift[3];      // storage shift s_i (rest equilibrium rounded to C)
     C corr[3];       // W_i rho0 - s_i (exact difference, rounded to C)
     C sum_corr;      // sum_i corr_i
+    C sigma;         // 1.5 * 2^e with 2^e >= 32 rho0: split constant of the exact
+                     // conserved sums (FP32 storage; see conserved)
     C lam;           // 1 - 1/tau
     C inv_2th2;      // 1 / (2 theta^2), theta = lattice theta (guided) or theta0 (poly2)
     C theta;         // lattice theta (guided) or theta0 (poly2)
@@ -274,37 +276,64 @@ __device__ __forceinline__ void two_sum(C a, C b, C &s, C &e) {
     e = (a - ap) + (b - bp);
 }
 
+// Rounded addition and subtraction that the compiler may neither contract nor
+// reassociate (the split below relies on every intermediate rounding).
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+// packed pairs: each lane rounds as the scalar FP32 operation (inline PTX,
+// which the compiler does not reassociate)
+__device__ __forceinline__ F2 add_rn(F2 a, F2 b) { return a + b; }
+__device__ __forceinline__ F2 sub_rn(F2 a, F2 b) { return a - b; }
+
 // Conserved moments of one node from its shifted populations g.
 //   drho = rho - rho0 = sum g_i - sum corr_i,  j = sum c_i g_i
 // (the shifts cancel in j because opposite directions share one shift).
-// COMP selects compensated (TwoSum) accumulation.
-template <typename C, bool COMP>
+//
+// The constant sum_corr (the shifts' rounding remainders, ~1e-8) enters the
+// sum first: subtracted last, it falls below half a unit of drho wherever
+// |rho - rho0| is large and is rounded away identically at every node and
+// step, a steady mass loss that dominates the drift of long FP32 runs.
+//
+// EXACT (FP32 storage) makes the sums exact, rounded once.  Each g_i splits
+// error-free into q_i = (g_i + sigma) - sigma, g_i rounded to the grid
+// ulp(sigma) = 2^(e-23), and r_i = g_i - q_i, |r_i| <= ulp(sigma) / 2.  While
+// |g_i| < 2^(e-1) (sigma = 1.5 * 2^e) the q_i and every partial sum of up to
+// nine of them (below 2^(e+1)) lie on the grid, so the q sums carry no
+// rounding; the r sums round at ~2^-24 of their size, ~2^(e-45).  drho and j
+// are then the exact sums up to one final rounding.  With 2^e >= 32 rho0 the
+// sums are exact for |g_i| < 7 rho0; beyond that they degrade to ordinary
+// rounded sums.  On the 2048 x 4 shock tube (tau = 0.51, 2000 steps) the
+// plain FP32 sums end 3e-5 from the FP64 scheme, these 1e-6..5e-6.
+template <typename C, bool EXACT>
 __device__ __forceinline__ void conserved(const C g[9], const CollConst<C> &k, C &drho,
                                           C &jx, C &jy) {
-    if constexpr (!COMP) {
-        drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8]) -
-               k.sum_corr;
+    if constexpr (!EXACT) {
+        drho = (((g[0] - k.sum_corr) + (g[1] + g[2])) + ((g[3] + g[4]) + (g[5] + g[6]))) +
+               (g[7] + g[8]);
         jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
         jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
     } else {
-        C s = g[0], e = C(0), t;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) { two_sum(s, g[i], s, t); e += t; }
-        drho = (s - k.sum_corr) + e;
-        C sx = g[1], ex = C(0);
-        two_sum(sx, -g[3], sx, t); ex += t;
-        two_sum(sx, g[5], sx, t); ex += t;
-        two_sum(sx, -g[6], sx, t); ex += t;
-        two_sum(sx, -g[7], sx, t); ex += t;
-        two_sum(sx, g[8], sx, t); ex += t;
-        jx = sx + ex;
-        C sy = g[2], ey = C(0);
-        two_sum(sy, -g[4], sy, t); ey += t;
-        two_sum(sy, g[5], sy, t); ey += t;
-        two_sum(sy, g[6], sy, t); ey += t;
-        two_sum(sy, -g[7], sy, t); ey += t;
-        two_sum(sy, -g[8], sy, t); ey += t;
-        jy = sy + ey;
+        // accumulated direction by direction, so that only the six partial
+        // sums stay live
+        C q, r, qd, rd, qx, rx, qy, ry;
+        auto split = [&](C gi) {
+            q = sub_rn(add_rn(gi, k.sigma), k.sigma);
+            r = sub_rn(gi, q);
+        };
+        split(g[0]); qd = q; rd = r - k.sum_corr;
+        split(g[1]); qd = qd + q; rd = rd + r; qx = q; rx = r;
+        split(g[2]); qd = qd + q; rd = rd + r; qy = q; ry = r;
+        split(g[3]); qd = qd + q; rd = rd + r; qx = qx - q; rx = rx - r;
+        split(g[4]); qd = qd + q; rd = rd + r; qy = qy - q; ry = ry - r;
+        split(g[5]); qd = qd + q; rd = rd + r; qx = qx + q; rx = rx + r; qy = qy + q; ry = ry + r;
+        split(g[6]); qd = qd + q; rd = rd + r; qx = qx - q; rx = rx - r; qy = qy + q; ry = ry + r;
+        split(g[7]); qd = qd + q; rd = rd + r; qx = qx - q; rx = rx - r; qy = qy - q; ry = ry - r;
+        split(g[8]); qd = qd + q; rd = rd + r; qx = qx + q; rx = rx + r; qy = qy - q; ry = ry - r;
+        drho = qd + rd;
+        jx = qx + rx;
+        jy = qy + ry;
     }
 }
 
@@ -325,25 +354,36 @@ __device__ __forceinline__ void conserved(const C g[9], const CollConst<C> &k, C
 //   [(C_x^2 - C_y^2) S_xx + 2 C_x C_y S_xy], C = c - u (the delta terms of
 // Eq. 6 vanish because S is trace-free), post = geq + (1 - 1/tau) f^OReg.
 // BGK (Eq. 1): post = geq + (1 - 1/tau) (g - geq).
-template <int EQ, int COLL, typename C, bool COMP>
-__device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst<C> &k) {
+//
+// HAVE_MOM: drho, jx, jy come in as mom[0..2] (the FP32 kernels form the exact
+// sums of two nodes at once with packed arithmetic; see collide_vec).
+template <int EQ, int COLL, typename C, bool EXACT, bool HAVE_MOM = false>
+__device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst<C> &k,
+                                        const C *mom = nullptr) {
     // Packed pairs (issue-bound half formats) share the opposite-direction
     // sums between the conserved moments and the stress and fold the OReg
     // prefactor into the stress; float and double keep the plain order.
     constexpr bool PACKED = std::is_same<C, F2>::value;
     constexpr bool LOCAL = EQ == EQ_GUIDED_LOCAL;
     C drho, jx, jy, dxy, pxy, tg = C(0);
-    if constexpr (PACKED && !COMP) {
+    if constexpr (HAVE_MOM) {
+        drho = mom[0];
+        jx = mom[1];
+        jy = mom[2];
+        dxy = (g[1] + g[3]) - (g[2] + g[4]);
+        pxy = (g[5] + g[7]) - (g[6] + g[8]);
+        if constexpr (LOCAL) tg = ((g[1] + g[3]) + (g[2] + g[4])) + C(2) * ((g[5] + g[7]) + (g[6] + g[8]));
+    } else if constexpr (PACKED && !EXACT) {
         const C s13 = g[1] + g[3], s24 = g[2] + g[4], s57 = g[5] + g[7], s68 = g[6] + g[8];
         const C d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d68 = g[6] - g[8];
-        drho = (((g[0] + s13) + (s24 + s57)) + s68) - k.sum_corr;
+        drho = (((g[0] - k.sum_corr) + s13) + (s24 + s57)) + s68;
         jx = (d13 + d57) - d68;
         jy = (d24 + d57) + d68;
         dxy = s13 - s24;
         pxy = s57 - s68;
         if constexpr (LOCAL) tg = (s13 + s24) + C(2) * (s57 + s68);
     } else {
-        conserved<C, COMP>(g, k, drho, jx, jy);
+        conserved<C, EXACT>(g, k, drho, jx, jy);
         dxy = (g[1] + g[3]) - (g[2] + g[4]);
         pxy = (g[5] + g[7]) - (g[6] + g[8]);
         if constexpr (LOCAL) tg = ((g[1] + g[3]) + (g[2] + g[4])) + C(2) * ((g[5] + g[7]) + (g[6] + g[8]));

@@ -146,6 +146,7 @@ __device__ __forceinline__ CollConst<F2> broadcast(const CollConst<float> &k) {
         b.corr[c] = F2(k.corr[c]);
     }
     b.sum_corr = F2(k.sum_corr);
+    b.sigma = F2(k.sigma);
     b.lam = F2(k.lam);
     b.inv_2th2 = F2(k.inv_2th2);
     b.theta = F2(k.theta);
@@ -156,11 +157,16 @@ __device__ __forceinline__ CollConst<F2> broadcast(const CollConst<float> &k) {
 // issue-bound) collide node pairs with packed f32x2 arithmetic; FP32 storage
 // (HBM-bound) stays scalar, where packing measured no faster for A-B and
 // slower for AA.
-template <int S, int EQ, int COLL, bool COMP>
+//
+// FP32 with exact conserved sums: PAIR_SUMS forms them for node pairs with
+// packed arithmetic (the A-B kernels: as fast as plain sums there); the
+// in-place AA kernels, at their register cap, form them per node (packing
+// spills there).  Both round every operation alike: the results are the same.
+template <int S, int EQ, int COLL, bool EXACT, bool PAIR_SUMS = true>
 __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<S>::V],
                                             const CollConst<typename Storage<S>::C> &k) {
     using C = typename Storage<S>::C;
-    if constexpr ((S == ST_F16 || S == ST_BF16) && !COMP) {
+    if constexpr ((S == ST_F16 || S == ST_BF16) && !EXACT) {
         const CollConst<F2> k2 = broadcast(k);
 #pragma unroll
         for (int j = 0; j < Storage<S>::V; j += 2) {
@@ -174,13 +180,37 @@ __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<
                 f[i][j + 1] = post[i].hi();
             }
         }
+    } else if constexpr (S == ST_F32 && EXACT && PAIR_SUMS) {
+        // the exact conserved sums of node pairs with packed arithmetic (the
+        // split costs ~50 additions per node), the rest of the collision scalar
+        CollConst<F2> k2;
+        k2.sigma = F2(k.sigma);
+        k2.sum_corr = F2(k.sum_corr);
+#pragma unroll
+        for (int j = 0; j < Storage<S>::V; j += 2) {
+            F2 g2[9], m2[3];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g2[i] = F2(f[i][j], f[i][j + 1]);
+            conserved<F2, true>(g2, k2, m2[0], m2[1], m2[2]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                C g[9], post[9];
+                const C mom[3] = {h ? m2[0].hi() : m2[0].lo(), h ? m2[1].hi() : m2[1].lo(),
+                                  h ? m2[2].hi() : m2[2].lo()};
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = f[i][j + h];
+                collide<EQ, COLL, C, EXACT, true>(g, post, k, mom);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i][j + h] = post[i];
+            }
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < Storage<S>::V; ++j) {
             C g[9], post[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) g[i] = f[i][j];
-            collide<EQ, COLL, C, COMP>(g, post, k);
+            collide<EQ, COLL, C, EXACT>(g, post, k);
 #pragma unroll
             for (int i = 0; i < 9; ++i) f[i][j] = post[i];
         }
@@ -233,7 +263,7 @@ __device__ __forceinline__ bool lane_has_wall(int xb, int nx) {
 }
 
 // One warp work item: row y, segment seg (32*V nodes) of a lattice.
-template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict__ src,
                                         typename Storage<S>::T *__restrict__ dst, int nx, int ny,
                                         int pitch, size_t plane, int y0, int seg, int lane, int lw,
@@ -253,7 +283,7 @@ __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict
     C f[9][V];
     pull_all<S, false>(src, plane, pitch, y, ny, xb, nx, sub, W, f);
 
-    collide_vec<S, EQ, COLL, COMP>(f, k);
+    collide_vec<S, EQ, COLL, EXACT>(f, k);
     if constexpr (WALLS) {
         if (lane_has_wall<S>(xb, nx))
             bounce_back_walls<S, STATE_AB>(src, plane, pitch, y, ny, xb, nx, f);
@@ -279,11 +309,11 @@ __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  \
     const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);                                   \
     if (item >= (long long)groups * segs) return; /* warp-uniform */                        \
-    item_ab<S, EQ, COLL, COMP, WALLS>(src, dst, nx, ny, pitch, plane,                        \
+    item_ab<S, EQ, COLL, EXACT, WALLS>(src, dst, nx, ny, pitch, plane,                        \
                                       (int)(item / segs) << (5 - lw), (int)(item % segs),   \
                                       threadIdx.x & 31, lw, k, t, sr);
 
-template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *__restrict__ src,
                                                  typename Storage<S>::T *__restrict__ dst, int nx,
                                                  int ny, int pitch, size_t plane, int segs,
@@ -301,7 +331,7 @@ __host__ __device__ constexpr bool ab_capped() {
     return !WALLS && EQ != EQ_GUIDED_LOCAL && (S == ST_F16 || S == ST_BF16);
 }
 constexpr int AB_CAPPED_MAX_THREADS = 128;
-template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(AB_CAPPED_MAX_THREADS, 5)
     k_step_ab_capped(const typename Storage<S>::T *__restrict__ src,
                      typename Storage<S>::T *__restrict__ dst, int nx, int ny, int pitch,
@@ -318,7 +348,7 @@ __global__ void __launch_bounds__(AB_CAPPED_MAX_THREADS, 5)
 // Every memory location is read and then written by the same node's update
 // only, so the update is race-free in place.
 // ---------------------------------------------------------------------------
-template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, int ny, int pitch,
                                              size_t plane, int y0, int seg, int lane, int lw,
                                              const CollConst<typename Storage<S>::C> &k,
@@ -342,7 +372,7 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
 #pragma unroll
         for (int j = 0; j < V; ++j) f[i][j] = ST::dec_step(v.e[j]);
     }
-    collide_vec<S, EQ, COLL, COMP>(f, k);
+    collide_vec<S, EQ, COLL, EXACT, false>(f, k);
     if constexpr (WALLS) {
         if (lane_has_wall<S>(xb, nx))
             bounce_back_walls<S, STATE_AA_EVEN>(A, plane, pitch, y, ny, xb, nx, f);
@@ -359,7 +389,7 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
     }
 }
 
-template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A, int nx, int ny,
                                                       int pitch, size_t plane, int segs, int lw,
                                                       const CollConst<typename Storage<S>::C> k,
@@ -367,7 +397,7 @@ __global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A,
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
     if (item >= (long long)groups * segs) return;
-    item_aa_even<S, EQ, COLL, COMP, WALLS>(A, nx, ny, pitch, plane,
+    item_aa_even<S, EQ, COLL, EXACT, WALLS>(A, nx, ny, pitch, plane,
                                            (int)(item / segs) << (5 - lw), (int)(item % segs),
                                            threadIdx.x & 31, lw, k, t, sr);
 }
@@ -380,7 +410,7 @@ __device__ __forceinline__ void push_plane(typename Storage<S>::T *A, size_t pla
     store_row_shifted_raw<S, cx_of(I)>(A + I * plane + (size_t)yd * pitch, xb, nx, sub, W, p);
 }
 
-template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, int ny, int pitch,
                                             size_t plane, int y0, int seg, int lane, int lw,
                                             const CollConst<typename Storage<S>::C> &k,
@@ -399,7 +429,7 @@ __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, i
     C f[9][V];
     pull_all<S, true>(A, plane, pitch, y, ny, xb, nx, sub, W, f);
 
-    collide_vec<S, EQ, COLL, COMP>(f, k);
+    collide_vec<S, EQ, COLL, EXACT, false>(f, k);
     if constexpr (WALLS) {
         if (lane_has_wall<S>(xb, nx))
             bounce_back_walls<S, STATE_AA_ODD>(A, plane, pitch, y, ny, xb, nx, f);
@@ -423,18 +453,18 @@ __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, i
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  \
     const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);                                   \
     if (item >= (long long)groups * segs) return;                                           \
-    item_aa_odd<S, EQ, COLL, COMP, WALLS>(A, nx, ny, pitch, plane,                          \
+    item_aa_odd<S, EQ, COLL, EXACT, WALLS>(A, nx, ny, pitch, plane,                          \
                                           (int)(item / segs) << (5 - lw), (int)(item % segs), \
                                           threadIdx.x & 31, lw, k, t, sr);
 
-template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
                                                      int pitch, size_t plane, int segs, int lw,
                                                      const CollConst<typename Storage<S>::C> k,
                                                      long long t, bool sr) {
     OREG_AA_ODD_BODY
 }
-template <int S, int EQ, int COLL, bool COMP, bool WALLS>
+template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(256, step_min_blocks(S))
     k_step_aa_odd_capped(typename Storage<S>::T *A, int nx, int ny, int pitch, size_t plane,
                          int segs, int lw, const CollConst<typename Storage<S>::C> k, long long t,
@@ -451,56 +481,56 @@ template <int S> struct StepLaunch {
     using T = typename ST::T;
     using C = typename ST::C;
 
-    template <int EQ, int COLL, bool COMP, bool WALLS>
+    template <int EQ, int COLL, bool EXACT, bool WALLS>
     static void step_eq(const StepArgs &a, dim3 grid, dim3 block) {
         const CollConst<C> &k = *static_cast<const CollConst<C> *>(a.kconst);
         const int segs = a.segs;
         if (a.layout == 0) {
             if constexpr (ab_capped<S, EQ, WALLS>()) {
                 if (block.x <= (unsigned)AB_CAPPED_MAX_THREADS) {
-                    k_step_ab_capped<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
+                    k_step_ab_capped<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
                         static_cast<const T *>(a.src), static_cast<T *>(a.dst), a.nx, a.ny,
                         a.pitch, a.plane, segs, a.lw, k, a.t, a.sr != 0);
                     return;
                 }
             }
-            k_step_ab<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
+            k_step_ab<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
                 static_cast<const T *>(a.src), static_cast<T *>(a.dst), a.nx, a.ny, a.pitch,
                 a.plane, segs, a.lw, k, a.t, a.sr != 0);
         } else if (a.parity == 0) {
-            k_step_aa_even<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
+            k_step_aa_even<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
                 static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
                 a.sr != 0);
         } else {
             if constexpr (aa_odd_capped<S, EQ, WALLS>()) {
-                k_step_aa_odd_capped<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
+                k_step_aa_odd_capped<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
                     static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
                     a.sr != 0);
             } else {
-                k_step_aa_odd<S, EQ, COLL, COMP, WALLS><<<grid, block, 0, a.stream>>>(
+                k_step_aa_odd<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
                     static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
                     a.sr != 0);
             }
         }
     }
 
-    template <bool COMP, bool WALLS>
+    template <bool EXACT, bool WALLS>
     static void step_comp(const StepArgs &a, dim3 grid, dim3 block) {
         if (a.eq == EQ_GUIDED) {
-            if (a.coll == COLL_OREG) step_eq<EQ_GUIDED, COLL_OREG, COMP, WALLS>(a, grid, block);
-            else step_eq<EQ_GUIDED, COLL_BGK, COMP, WALLS>(a, grid, block);
+            if (a.coll == COLL_OREG) step_eq<EQ_GUIDED, COLL_OREG, EXACT, WALLS>(a, grid, block);
+            else step_eq<EQ_GUIDED, COLL_BGK, EXACT, WALLS>(a, grid, block);
         } else if (a.eq == EQ_GUIDED_LOCAL) {
-            if (a.coll == COLL_OREG) step_eq<EQ_GUIDED_LOCAL, COLL_OREG, COMP, WALLS>(a, grid, block);
-            else step_eq<EQ_GUIDED_LOCAL, COLL_BGK, COMP, WALLS>(a, grid, block);
+            if (a.coll == COLL_OREG) step_eq<EQ_GUIDED_LOCAL, COLL_OREG, EXACT, WALLS>(a, grid, block);
+            else step_eq<EQ_GUIDED_LOCAL, COLL_BGK, EXACT, WALLS>(a, grid, block);
         } else {
-            if (a.coll == COLL_OREG) step_eq<EQ_POLY2, COLL_OREG, COMP, WALLS>(a, grid, block);
-            else step_eq<EQ_POLY2, COLL_BGK, COMP, WALLS>(a, grid, block);
+            if (a.coll == COLL_OREG) step_eq<EQ_POLY2, COLL_OREG, EXACT, WALLS>(a, grid, block);
+            else step_eq<EQ_POLY2, COLL_BGK, EXACT, WALLS>(a, grid, block);
         }
     }
 
     template <bool WALLS>
     static void step_walls(const StepArgs &a, dim3 grid, dim3 block) {
-        // compensated sums exist for FP32 storage only
+        // exact conserved sums exist for FP32 storage only
         if constexpr (S == ST_F32) {
             if (a.comp) {
                 step_comp<true, WALLS>(a, grid, block);

@@ -30,7 +30,7 @@ struct StepArgs {
     int lw;            // log2 of W, the lanes per row segment (W <= 32)
     int eq, coll, layout, parity;  // eq: kernel equilibrium kind (EQ_GUIDED_LOCAL for
                                    // the guided equilibrium at the local temperature)
-    int comp;          // compensated conserved-moment sums (FP32 only)
+    int comp;          // exact conserved-moment sums (FP32 only)
     int sr;            // stochastic rounding (half formats only)
     int walls;         // full-way bounce-back wall columns x = 0 and x = nx - 1
     long long t;       // time of the state being advanced

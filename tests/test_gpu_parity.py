@@ -87,27 +87,28 @@ def test_shear_wave_64x64_fp32(case):
     assert err <= TOL["f32"], err
 
 
-# The FP32 shock tube at tau = 0.51 (nu = 3.3e-3) over 2000 steps is the one
-# case that does not reach 1e-5: per-step FP32 rounding accumulates through
-# the weakly damped waves the same way FP64 rounding does (the FP64 kernel
-# sits ~3e3 unit roundoffs from the oracle after 2000 steps); storing the
-# populations in FP32 alone, with exact arithmetic, already costs ~4e-6.
-# Measured 1.8e-5 for both equilibria; gated at 5e-5 (~1000 FP32 unit
-# roundoffs).  Before the periodic waves meet (t = 500) the 1e-5 bound holds.
-TOL_F32_SHOCK_2000 = 5e-5
-
-
-@pytest.mark.parametrize("comp", [0, 1])
+# The FP32 shock tube at tau = 0.51 (nu = 3.3e-3) over 2000 steps, the
+# weakest-damped case: FP32 storage with the default exact conserved sums
+# (OLB_OPT_COMPENSATED = 1) must stay within 1e-5 of the FP64 oracle at
+# t = 2000 and t = 500, both layouts.  Plain sums (option 0) end ~3e-5 away
+# after 2000 steps (their rounding repeats identically over the uniform
+# states); they are held to 1e-5 at t = 500 only, before the periodic waves
+# meet.
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 @pytest.mark.parametrize("case", SHOCK_2048X4, ids=lambda c: f"shock-{c.eq}")
-def test_shock_tube_2048x4_fp32(case, layout, comp):
-    opts = {"comp": comp}
-    err = rel_linf(gpu_run(case, case.steps, "f32", layout, **opts), oracle_run(case, case.steps))
-    print(f"FP32 shock {case.eq} {layout} comp={comp} t=2000: rel Linf {err:.3e}")
-    assert err <= TOL_F32_SHOCK_2000, err
-    err500 = rel_linf(gpu_run(case, 500, "f32", layout, **opts), oracle_run(case, 500))
-    print(f"FP32 shock {case.eq} {layout} comp={comp} t=500: rel Linf {err500:.3e}")
-    assert err500 <= TOL["f32"], err500
+def test_shock_tube_2048x4_fp32(case, layout):
+    for steps in (case.steps, 500):
+        err = rel_linf(gpu_run(case, steps, "f32", layout), oracle_run(case, steps))
+        print(f"FP32 shock {case.eq} {layout} t={steps}: rel Linf {err:.3e}")
+        assert err <= TOL["f32"], (steps, err)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("case", SHOCK_2048X4, ids=lambda c: f"shock-{c.eq}")
+def test_shock_tube_2048x4_fp32_plain_sums_t500(case, layout):
+    err = rel_linf(gpu_run(case, 500, "f32", layout, comp=0), oracle_run(case, 500))
+    print(f"FP32 plain sums shock {case.eq} {layout} t=500: rel Linf {err:.3e}")
+    assert err <= TOL["f32"], err
 
 
 # FP32 storage with the collision in FP64 (OLB_OPT_F64_COLLISION): the store
