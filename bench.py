@@ -425,22 +425,26 @@ def run_native(args):
 
 def batched_section(args):
     """Batched workload: 512 independent uneven lattices, FP16 storage (stochastic
-    rounding) / FP32 compute, autotuned batch, one CUDA-graph replay per 100
-    steps; against serial plain FP32 single-lattice solves of the same set."""
+    rounding) / FP32 compute, autotuned batch (layout, block shape, grid, row
+    groups per work item, steps per CUDA-graph replay); against serial plain
+    FP32 single-lattice solves of the same set."""
     import numpy as np
     import torch
     from paper_2501_16000_gb300 import workloads as W
     from paper_2501_16000_gb300.analysis import measure_decay
     from paper_2501_16000_gb300.batch import BatchEngine, autotune, work_items
     from paper_2501_16000_gb300.engine import Lattice
-    steps, K = args.batch_steps, 100
+    steps = args.batch_steps
     cases = W.batch_mix(count=args.batch_count, seed=1, steps=steps)
     nodes = sum(c.nodes for c in cases)
-    tuned = autotune(cases, "f16", steps=20, use_cache=False)
-    items = sum(work_items(c.nx, c.ny, "f16") for c in cases)
+    t_tune = time.perf_counter()
+    tuned = autotune(cases, "f16", use_cache=False)
+    t_tune = time.perf_counter() - t_tune
+    K, R = tuned["steps_per_launch"], tuned["item_row_groups"]
+    items = sum(work_items(c.nx, c.ny, "f16", R) for c in cases)
     with BatchEngine("f16", tuned["layout"], max_lattices=len(cases), max_items=items,
                      steps_per_launch=K, warps_per_block=tuned["warps_per_block"],
-                     blocks_per_sm=tuned["blocks_per_sm"]) as eng:
+                     blocks_per_sm=tuned["blocks_per_sm"], item_row_groups=R) as eng:
         # warm-up solve (graph capture), then the timed solve on fresh states
         for rep in range(2):
             lats = [eng.new_lattice(c) for c in cases]
@@ -484,6 +488,7 @@ def batched_section(args):
                     f"(stochastic rounding) / FP32 compute, graph replay per {K} steps",
         "nodes": nodes, "solves_per_s": round(len(cases) / dt, 2), "seconds": round(dt, 4),
         "mlups": round(nodes * steps / dt / 1e6, 1), "tuned": tuned,
+        "tune_seconds": round(t_tune, 1),
         "baseline_fp32_serial": {"solves_per_s": round(len(cases) / dt_ser, 2),
                                  "seconds": round(dt_ser, 4),
                                  "mlups": round(nodes * steps / dt_ser / 1e6, 1)},
@@ -505,9 +510,11 @@ def serving_section(args, batched):
     mean_work = float(np.mean([r.lattice.nodes * r.lattice.steps for r in unit]))
     capacity = batched["mlups"] * 1e6 / mean_work            # requests per second
     rate = 0.8 * capacity
-    srv = Server("f16", batched["tuned"]["layout"], budget_bytes=120e9, steps_per_launch=100,
-                 warps_per_block=batched["tuned"]["warps_per_block"],
-                 blocks_per_sm=batched["tuned"]["blocks_per_sm"])
+    tuned = batched["tuned"]
+    srv = Server("f16", tuned["layout"], budget_bytes=120e9,
+                 steps_per_launch=tuned["steps_per_launch"],
+                 warps_per_block=tuned["warps_per_block"], blocks_per_sm=tuned["blocks_per_sm"],
+                 item_row_groups=tuned["item_row_groups"])
     res, wall = srv.run(unit, time_scale=1.0 / rate)
     stats = summarize(res, wall, "continuous batching, FP16 storage")
     stats.update({"rounds": srv.rounds, "peak_inflight": srv.peak_inflight,

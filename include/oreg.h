@@ -151,8 +151,8 @@ typedef enum {
     OLB_OPT_F64_COLLISION = 4
 } olb_option;
 
-/* Version of this ABI (bumped on incompatible change); 3 since
- * olb_params.theta_mode. */
+/* Version of this ABI (bumped on incompatible change); 4 since
+ * olb_batch_params.item_row_groups. */
 int32_t olb_abi_version(void);
 
 /* Bytes of device memory the populations of a lattice with these
@@ -261,9 +261,15 @@ olb_status olb_wave_mode(olb_lattice *lat, int32_t m, int32_t n, double *a_sin,
  * launches are captured once in a CUDA graph and replayed per round.  Each
  * member keeps its own size, relaxation time, temperature, equilibrium and
  * collision; all members share the batch's storage format and layout and
- * must have been created on the batch's stream.  Joining and leaving rewrite
- * the device tables only (the graph is captured once).  A member is advanced
- * exactly the number of steps it was added with, then idles until removed.
+ * must have been created on the batch's stream.  Members are grouped into
+ * slots of one kernel (walls, equilibrium kind, collision) and one class of
+ * collision constants (the same theta, rho0 and equilibrium; tau is per
+ * member), and every step launches one kernel per slot, whose class constants
+ * are a launch parameter.  Joining and leaving rewrite the device tables
+ * only; the graph is captured again when a member brings a new slot (at most
+ * 64 slots are in use at a time: olb_batch_add returns OLB_ERR_NOMEM beyond).
+ * A member is advanced exactly the number of steps it was added with, then
+ * idles until removed.
  * Results are bitwise those of olb_step on the same lattice: each node's
  * update depends only on that lattice's state.
  * ---------------------------------------------------------------------- */
@@ -274,16 +280,21 @@ typedef struct {
     int32_t layout;            /* olb_layout of every member */
     int32_t max_lattices;      /* descriptor capacity */
     int64_t max_items;         /* work-item capacity: sum over members of
-                                  ceil(ceil(ny / (32 / W)) / 4) * ceil(nx / (W * V)),
-                                  V = 16 / element size, W the smallest power
-                                  of two <= 32 with W * V >= nx (an item is up
-                                  to 4 groups of 32 / W rows of one segment) */
+                                  ceil(ceil(ny / (32 / W)) / R) * ceil(nx / (W * V)),
+                                  V = 16 / element size, W the lanes per row
+                                  segment (a power of two <= 32, the one with
+                                  the fewest warp passes over the lattice), R
+                                  = item_row_groups (an item is up to R groups
+                                  of 32 / W rows of one segment) */
     int32_t steps_per_launch;  /* K: time steps per graph replay (1..10000) */
     int32_t warps_per_block;   /* 1, 2 or 4 */
     int32_t blocks_per_sm;     /* persistent grid = blocks_per_sm x SMs;
                                   0 = the kernel's occupancy limit */
     void *cuda_stream;         /* stream of the batch and of every member;
                                   NULL: the library creates and owns one */
+    int32_t item_row_groups;   /* R: row groups per work item (1..64); a warp
+                                  reads the member's descriptor once per item;
+                                  0 = 4 */
 } olb_batch_params;
 
 olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out);

@@ -3,8 +3,9 @@ steps_per_launch steps per CUDA-graph replay (C ABI ``olb_batch_*``).
 
 ``BatchEngine`` owns the batch and a torch stream; its lattices are created on
 that stream with torch-allocated population memory.  ``autotune`` picks the
-layout, warps per block and persistent-grid size for a workload by timing
-short runs, and caches the choice per (storage, size class).
+layout, warps per block, persistent-grid size, row groups per work item and
+steps per graph replay for a workload by timing graph replays, and caches the
+choice per (ABI, storage, size class).
 """
 from __future__ import annotations
 
@@ -12,6 +13,7 @@ import ctypes
 import json
 import math
 import os
+import statistics
 import time
 
 from . import binding as B
@@ -20,7 +22,7 @@ from .engine import LAYOUT, STORAGE, Lattice
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
-ITEM_ROW_GROUPS = 4
+ITEM_ROW_GROUPS = 4   # the library's default row groups per work item
 
 
 def segment_lanes(nx: int, ny: int, v: int) -> int:
@@ -35,26 +37,28 @@ def segment_lanes(nx: int, ny: int, v: int) -> int:
     return best
 
 
-def work_items(nx: int, ny: int, storage: str) -> int:
+def work_items(nx: int, ny: int, storage: str, row_groups: int = ITEM_ROW_GROUPS) -> int:
     """Warp work items of one lattice: a warp pass covers a row group of 32/W
     rows of one W-lane row segment (``segment_lanes``); an item is up to
-    ITEM_ROW_GROUPS row groups of one segment."""
+    `row_groups` row groups of one segment."""
     v = 16 // {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[storage]
     w = segment_lanes(nx, ny, v)
-    return math.ceil(math.ceil(ny / (32 // w)) / ITEM_ROW_GROUPS) * math.ceil(nx / (w * v))
+    return math.ceil(math.ceil(ny / (32 // w)) / row_groups) * math.ceil(nx / (w * v))
 
 
 class BatchEngine:
     def __init__(self, storage="f16", layout="ab", max_lattices=1024, max_items=1 << 22,
-                 steps_per_launch=100, warps_per_block=4, blocks_per_sm=0, stream=None):
+                 steps_per_launch=100, warps_per_block=4, blocks_per_sm=0, stream=None,
+                 item_row_groups=ITEM_ROW_GROUPS):
         import torch
         self.storage, self.layout = storage, layout
         self.steps_per_launch = int(steps_per_launch)
+        self.item_row_groups = int(item_row_groups)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.params = B.olb_batch_params(STORAGE[storage], LAYOUT[layout], int(max_lattices),
                                          int(max_items), int(steps_per_launch),
                                          int(warps_per_block), int(blocks_per_sm),
-                                         self.stream.cuda_stream)
+                                         self.stream.cuda_stream, int(item_row_groups))
         h = ctypes.c_void_p()
         B.check(B.load().olb_batch_create(ctypes.byref(self.params), ctypes.byref(h)),
                 "olb_batch_create")
@@ -117,47 +121,108 @@ def size_class(cases) -> str:
     return f"n{len(cases)}-2^{int(math.log2(max(nodes, 1)))}"
 
 
-def autotune(cases, storage="f16", steps=20, candidates=None, use_cache=True, verbose=False):
-    """Times `steps` steps of the whole workload for each candidate
-    (layout, warps_per_block, blocks_per_sm) and returns the fastest as a dict
-    with its measured ms per step.  Results are cached per (storage, size class)."""
+# Search space of the tuner.  The stages run in this order, each over one
+# group of parameters with the best values found so far for the others:
+# (layout, warps per block, blocks per SM), then row groups per work item,
+# then steps per graph replay.
+TUNE_STAGES = (
+    {"layout": ("ab", "aa"), "warps_per_block": (1, 2, 4), "blocks_per_sm": (0, 1, 2)},
+    {"item_row_groups": (1, 2, 4, 8)},
+    {"steps_per_launch": (25, 50, 100, 200)},
+)
+TUNE_START = {"layout": "ab", "warps_per_block": 4, "blocks_per_sm": 0,
+              "item_row_groups": ITEM_ROW_GROUPS, "steps_per_launch": 50}
+
+
+def _grid(stage: dict):
+    keys = list(stage)
+    out = [{}]
+    for k in keys:
+        out = [dict(o, **{k: v}) for o in out for v in stage[k]]
+    return out
+
+
+def measure_replays(cases, storage: str, cfg: dict, repeats: int, lattices=None) -> list:
+    """ms per step of `repeats` timed graph replays (after one untimed replay,
+    which captures the graph) of the whole workload in the configuration
+    `cfg`.  `lattices` maps a layout to lattices to reuse (created on first
+    use on a shared stream, so that they can move between batches)."""
     import torch
-    # the key carries the library's ABI version: kernels and limits change with it
+    lattices = {} if lattices is None else lattices
+    K = int(cfg["steps_per_launch"])
+    stream = lattices.setdefault("_stream", torch.cuda.Stream())
+    items = sum(work_items(c.nx, c.ny, storage, cfg["item_row_groups"]) for c in cases)
+    with BatchEngine(storage, cfg["layout"], max_lattices=len(cases), max_items=items,
+                     steps_per_launch=K, warps_per_block=cfg["warps_per_block"],
+                     blocks_per_sm=cfg["blocks_per_sm"], item_row_groups=cfg["item_row_groups"],
+                     stream=stream) as eng:
+        if cfg["layout"] not in lattices:
+            lattices[cfg["layout"]] = [eng.new_lattice(c) for c in cases]
+        lats = lattices[cfg["layout"]]
+        for lat in lats:
+            eng.add(lat, (repeats + 1) * K)
+        eng.run(1)
+        eng.wait()
+        out = []
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            eng.run(1)
+            eng.wait()
+            out.append((time.perf_counter() - t0) * 1e3 / K)
+        for lat in lats:
+            eng.remove(lat)
+    return out
+
+
+def autotune(cases, storage="f16", stages=TUNE_STAGES, start=None, repeats=3, use_cache=True,
+             cache_path=None, measure=None, verbose=False):
+    """Chooses the batch configuration for a workload: layout, warps per block,
+    blocks per SM, row groups per work item and steps per graph replay.
+
+    Each candidate is timed as the median ms per step of `repeats` graph
+    replays (``measure_replays``, or `measure(cfg) -> [ms, ...]`); the stages
+    of `stages` run in order, each keeping the others at the best values so
+    far.  The result (a dict of the five parameters plus ``ms_per_step`` and
+    ``candidates``, the number timed) is cached per (ABI version, storage,
+    size class) in `cache_path` (default: the build folder)."""
+    cache_path = _CACHE if cache_path is None else cache_path
     key = f"abi{B.ABI_VERSION}:{storage}:{size_class(cases)}"
     cache = {}
-    if use_cache and os.path.exists(_CACHE):
+    if use_cache and os.path.exists(cache_path):
         try:
-            cache = json.load(open(_CACHE))
+            with open(cache_path) as f:
+                cache = json.load(f)
         except ValueError:
             cache = {}
         if key in cache:
             return cache[key]
-    if candidates is None:
-        candidates = [(lay, w, b) for lay in ("ab", "aa") for w in (1, 2, 4) for b in (0, 1, 2)]
-    items = sum(work_items(c.nx, c.ny, storage) for c in cases)
-    best = None
-    for lay, w, b in candidates:
-        with BatchEngine(storage, lay, max_lattices=len(cases), max_items=items,
-                         steps_per_launch=steps, warps_per_block=w, blocks_per_sm=b) as eng:
-            lats = [eng.new_lattice(c) for c in cases]
-            for lat in lats:
-                eng.add(lat, 2 * steps)
-            eng.run(1)            # capture + warm-up round
-            eng.wait()
-            t0 = time.perf_counter()
-            eng.run(1)
-            eng.wait()
-            ms = (time.perf_counter() - t0) * 1e3 / steps
-            for lat in lats:
-                lat.close()
-        r = {"layout": lay, "warps_per_block": w, "blocks_per_sm": b, "ms_per_step": ms}
-        if verbose:
-            print(r, flush=True)
-        if best is None or ms < best["ms_per_step"]:
-            best = r
-    torch.cuda.synchronize()
+    pool = {}
+    if measure is None:
+        def measure(cfg):
+            return measure_replays(cases, storage, cfg, repeats, pool)
+    best = dict(TUNE_START if start is None else start)
+    best_ms, seen = None, {}
+    try:
+        for stage in stages:
+            for delta in _grid(stage):
+                cfg = dict(best, **delta)
+                ident = tuple(sorted(cfg.items()))
+                if ident not in seen:
+                    samples = list(measure(cfg))
+                    seen[ident] = statistics.median(samples)
+                    if verbose:
+                        print(cfg, [round(x, 4) for x in samples], flush=True)
+                if best_ms is None or seen[ident] < best_ms:
+                    best, best_ms = cfg, seen[ident]
+    finally:
+        for name, lats in pool.items():
+            if name != "_stream":
+                for lat in lats:
+                    lat.close()
+    result = dict(best, ms_per_step=best_ms, candidates=len(seen), repeats=repeats)
     if use_cache:
-        cache[key] = best
-        os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
-        json.dump(cache, open(_CACHE, "w"), indent=1)
-    return best
+        cache[key] = result
+        os.makedirs(os.path.dirname(cache_path) or ".", exist_ok=True)
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return result

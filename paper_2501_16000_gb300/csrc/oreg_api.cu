@@ -322,7 +322,7 @@ olb_status mode_tables(olb_lattice *L, int m, int n) {
 
 extern "C" {
 
-int32_t olb_abi_version(void) { return 3; }
+int32_t olb_abi_version(void) { return 4; }
 
 size_t olb_required_bytes(const olb_params *p) {
     if (validate(p) != OLB_OK) return 0;

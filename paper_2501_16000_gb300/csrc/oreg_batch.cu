@@ -47,24 +47,48 @@ olb_status bcuda(cudaError_t e, const char *what) {
      : (storage) == OLB_F16_SHIFTED ? fn##_f16(__VA_ARGS__)             \
                                     : fn##_bf16(__VA_ARGS__))
 
-// item groups: (walls, equilibrium kind, collision, parity class)
-constexpr int NGROUPS = 24;
+// Slots (one kernel and one constant class each) a batch tracks before it
+// compacts its slot list; work-item groups are (slot, parity class).
+constexpr int MAX_SLOTS = 64;
+constexpr int NGROUPS = 2 * MAX_SLOTS;
 
 // (walls, equilibrium kind, collision) of a lattice: its batch kernel
 int combo_index(const olb_lattice *L) {
     const int walls = L->p.boundary == OLB_BOUNDARY_WALLS_X;
     return (walls * 3 + kernel_eq(&L->p)) * 2 + L->p.coll;
 }
-unsigned combo_bit(const olb_lattice *L) { return 1u << combo_index(L); }
 
 struct Member {
     olb_lattice *lat;
     long long g_base, g_end;  // active global steps [g_base, g_end)
     long long t_base;         // lattice time at g_base
+    int slot;
 };
 
+// A slot: kernel combination and the class constants (lam zeroed).
+struct Slot {
+    int combo;
+    std::vector<char> k;
+};
+
+// The collision constants a lattice's batch kernel takes, with lam (per
+// lattice, from the descriptor) zeroed: the lattice's constant class.
+std::vector<char> class_constants(const olb_lattice *L) {
+    std::vector<char> out;
+    if (L->p.storage == OLB_F64) {
+        CollConst<double> k = L->kd;
+        k.lam = 0.0;
+        out.assign(reinterpret_cast<const char *>(&k), reinterpret_cast<const char *>(&k) + sizeof k);
+    } else {
+        CollConst<float> k = L->kf;
+        k.lam = 0.0f;
+        out.assign(reinterpret_cast<const char *>(&k), reinterpret_cast<const char *>(&k) + sizeof k);
+    }
+    return out;
+}
+
 template <typename C>
-void fill_desc(void *dst, const Member &m, const CollConst<C> &k) {
+void fill_desc(void *dst, const Member &m, C lam) {
     BatchDesc<C> d;
     std::memset(&d, 0, sizeof d);
     const olb_lattice *L = m.lat;
@@ -81,7 +105,7 @@ void fill_desc(void *dst, const Member &m, const CollConst<C> &k) {
     d.g_base = m.g_base;
     d.g_end = m.g_end;
     d.sr = L->sr;
-    d.k = k;
+    d.lam = lam;
     std::memcpy(dst, &d, sizeof d);
 }
 
@@ -97,39 +121,82 @@ struct olb_batch {
     // device tables
     char *d_descs;
     int4 *d_items;
-    int *d_groups;          // item offsets of the 24 (walls, eq kind, coll, parity class) groups
+    int *d_groups;          // item offsets of the (slot, parity class) groups
     long long *d_g;
     // host mirrors
     std::vector<Member> members;
+    std::vector<Slot> slots;   // slots in launch order (kept while the graph is valid)
     std::vector<char> h_descs;
     std::vector<int4> h_items;
     int *h_groups;          // pinned, NGROUPS + 1 entries
     long long G;            // global step counter at the start of the next round
     bool captured;
-    unsigned graph_combos;  // (walls, eq, coll) kernels the captured graph launches
+    int graph_slots;        // slots the captured graph launches
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
 
 namespace {
 
+void drop_graph(olb_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->captured = false;
+}
+
+// Slot of a member: an existing slot with its kernel and constants, else a
+// new one at the end (the captured graph then lacks it and is dropped).  When
+// the list is full, slots no member uses are removed (renumbering the rest)
+// and the graph is dropped too.
+int slot_for(olb_batch *b, const olb_lattice *L) {
+    const int combo = combo_index(L);
+    const std::vector<char> k = class_constants(L);
+    for (size_t s = 0; s < b->slots.size(); ++s)
+        if (b->slots[s].combo == combo && b->slots[s].k == k) return (int)s;
+    if ((int)b->slots.size() == MAX_SLOTS) {
+        std::vector<Slot> kept;
+        for (Member &m : b->members) {
+            int found = -1;
+            for (size_t s = 0; s < kept.size(); ++s)
+                if (kept[s].combo == b->slots[m.slot].combo && kept[s].k == b->slots[m.slot].k)
+                    found = (int)s;
+            if (found < 0) {
+                kept.push_back(b->slots[m.slot]);
+                found = (int)kept.size() - 1;
+            }
+            m.slot = found;
+        }
+        b->slots.swap(kept);
+        drop_graph(b);
+        for (size_t s = 0; s < b->slots.size(); ++s)
+            if (b->slots[s].combo == combo && b->slots[s].k == k) return (int)s;
+        if ((int)b->slots.size() == MAX_SLOTS) return -1;
+    }
+    b->slots.push_back(Slot{combo, k});
+    if (b->captured && (int)b->slots.size() > b->graph_slots) drop_graph(b);
+    return (int)b->slots.size() - 1;
+}
+
 olb_status upload(olb_batch *b) {
     const size_t nm = b->members.size();
     b->h_descs.assign(nm * b->desc_size, 0);
-    std::vector<int4> per_group[NGROUPS];
+    std::vector<std::vector<int4>> per_group(NGROUPS);
     for (size_t j = 0; j < nm; ++j) {
         const Member &m = b->members[j];
         const olb_lattice *L = m.lat;
-        if (L->p.storage == OLB_F64) fill_desc<double>(&b->h_descs[j * b->desc_size], m, L->kd);
-        else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf);
+        if (L->p.storage == OLB_F64) fill_desc<double>(&b->h_descs[j * b->desc_size], m, L->kd.lam);
+        else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf.lam);
         const int cls = (int)((m.t_base - m.g_base) & 1);
-        const int grp = combo_index(L) * 2 + cls;
+        const int grp = m.slot * 2 + cls;
         const int lw = segment_log2(L->p.nx, L->p.ny, L->V);
         const int segs = (L->p.nx + (L->V << lw) - 1) / (L->V << lw);
         const int rows = 32 >> lw;  // rows per row group (one warp pass)
         const int ngroups = (L->p.ny + rows - 1) / rows;
-        for (int q = 0; q < ngroups; q += BATCH_ITEM_ROW_GROUPS) {
-            const int count = std::min(BATCH_ITEM_ROW_GROUPS, ngroups - q);
+        const int R = b->p.item_row_groups;
+        for (int q = 0; q < ngroups; q += R) {
+            const int count = std::min(R, ngroups - q);
             for (int s = 0; s < segs; ++s)
                 per_group[grp].push_back(make_int4((int)j, q * rows, s, count));
         }
@@ -162,6 +229,8 @@ olb_status upload(olb_batch *b) {
 __global__ void k_batch_advance(long long *g, int K) { *g += K; }
 
 olb_status capture(olb_batch *b) {
+    std::vector<BatchSlot> slots(b->slots.size());
+    for (size_t s = 0; s < b->slots.size(); ++s) slots[s] = BatchSlot{b->slots[s].combo, b->slots[s].k.data()};
     BatchLaunch a{};
     a.descs = b->d_descs;
     a.items = b->d_items;
@@ -171,8 +240,8 @@ olb_status capture(olb_batch *b) {
     a.grid = b->grid;
     a.block = b->block;
     a.stream = b->stream;
-    a.combos = 0;
-    for (const Member &m : b->members) a.combos |= combo_bit(m.lat);
+    a.nslots = (int)slots.size();
+    a.slots = slots.data();
     B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
            "beginning graph capture");
     cudaError_t e = cudaSuccess;
@@ -194,7 +263,7 @@ olb_status capture(olb_batch *b) {
     b->graph = g;
     B_CUDA(cudaGraphInstantiate(&b->exec, g, 0), "instantiating batch graph");
     b->captured = true;
-    b->graph_combos = a.combos;
+    b->graph_slots = a.nslots;
     return OLB_OK;
 }
 
@@ -219,9 +288,13 @@ olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out) {
         return bfail(OLB_ERR_INVALID, "warps_per_block must be 1, 2 or 4");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32)
         return bfail(OLB_ERR_INVALID, "blocks_per_sm must be in [0, 32] (0 = occupancy limit)");
+    if (p->item_row_groups < 0 || p->item_row_groups > 64)
+        return bfail(OLB_ERR_INVALID, "item_row_groups must be in [0, 64] (0 = %d)",
+                     BATCH_ITEM_ROW_GROUPS);
     olb_batch *b = new (std::nothrow) olb_batch();
     if (!b) return bfail(OLB_ERR_NOMEM, "host allocation of the batch failed");
     b->p = *p;
+    if (b->p.item_row_groups == 0) b->p.item_row_groups = BATCH_ITEM_ROW_GROUPS;
     b->desc_size = BDISPATCH(p->storage, batch_desc_size);
     auto bail = [&](olb_status s) {
         olb_batch_destroy(b);
@@ -285,6 +358,12 @@ olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps) {
     m.g_base = b->G;
     m.g_end = b->G + nsteps;
     m.t_base = lat->t;
+    // a new slot (kernel or constant class) invalidates the captured graph,
+    // which is captured again on the next run
+    m.slot = slot_for(b, lat);
+    if (m.slot < 0)
+        return bfail(OLB_ERR_NOMEM, "batch members use more than %d (kernel, constant class) slots",
+                     MAX_SLOTS);
     b->members.push_back(m);
     olb_status st = upload(b);
     if (st != OLB_OK) {
@@ -293,14 +372,6 @@ olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps) {
         return st;
     }
     lat->batch = b;
-    if (b->captured && !(b->graph_combos & combo_bit(lat))) {
-        // the graph lacks this lattice's kernels: capture again on the next run
-        cudaGraphExecDestroy(b->exec);
-        cudaGraphDestroy(b->graph);
-        b->exec = nullptr;
-        b->graph = nullptr;
-        b->captured = false;
-    }
     return OLB_OK;
 }
 
@@ -364,8 +435,7 @@ olb_status olb_batch_destroy(olb_batch *b) {
         if (e != cudaSuccess) st = bcuda(e, "synchronising before destroy");
     }
     for (Member &m : b->members) m.lat->batch = nullptr;
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
+    drop_graph(b);
     if (b->d_descs) cudaFree(b->d_descs);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_groups) cudaFree(b->d_groups);

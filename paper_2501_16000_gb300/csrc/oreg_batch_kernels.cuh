@@ -31,46 +31,46 @@ template <typename C> struct BatchDesc {
     long long g_base;     // first global step the lattice takes part in
     long long g_end;      // first global step it no longer takes part in
     int sr;               // stochastic rounding of half formats
-    CollConst<C> k;
+    C lam;                // 1 - 1/tau of this lattice (the collision constants
+                          // but lam come from its constant class)
 };
 
-// Work items are grouped on the host by (walls, equilibrium kind, collision,
-// parity class): group = ((walls * 3 + eq) * 2 + coll) * 2 + c, with eq the
-// kernel's equilibrium kind (guided, polynomial, guided at the local
-// temperature) and
+// Lattices are grouped into slots: one (walls, equilibrium kind, collision)
+// kernel and one constant class, i.e. the same collision constants apart from
+// 1 - 1/tau (same theta, rho0 and equilibrium).  The class constants reach
+// the kernel as a launch parameter, like the single-lattice kernels' (the
+// compiler re-reads them from the parameter bank instead of holding them in
+// registers), and each lattice's lam comes from its descriptor.  Work items
+// are grouped by (slot, parity class): group = slot * 2 + c, with
 // c = (t_base - g_base) & 1 the lattice's fixed offset between its own time
 // and the global step, so that at global step g every lattice of class c has
-// time parity (g + c) & 1.  Each kernel below handles one (walls, eq, coll)
-// and, for the in-place layout, one parity: one item body per kernel keeps
-// register use at the single-lattice kernels' level.  groups[0..24] are the
-// item offsets of the 24 groups.  A batch launches only the kernels of the
-// (walls, eq, coll) combinations its members use (bit ((walls * 3 + eq) * 2
-// + coll) of BatchLaunch::combos).
+// time parity (g + c) & 1.  groups[0 .. 2 * slots] are the item offsets of
+// the groups; one launch per slot and step (per parity kernel for the in-place
+// layout) walks its items.
 enum { BATCH_AB = 0, BATCH_AA_EVEN = 1, BATCH_AA_ODD = 2 };
 
-// At most 128 threads x 3 blocks per SM (a 170-register cap): the per-lattice
-// constants come from the descriptor in global memory rather than the
-// parameter bank, and left to itself the compiler keeps them all in registers
-// (150-180 for half storage), halving occupancy.  On 512 mixed FP16 lattices
-// tighter caps that buy more warps spill and run slower (128 registers: -10%,
-// 144: -4%; the kernel uses ~155 at this bound).
+// At most 128 threads x 4 blocks per SM (a 128-register cap, 16 warps): with
+// the class constants in the parameter bank the half-format kernels fit in
+// 128 registers without spilling (158 when the constants came from the
+// descriptor in global memory, 12 warps).
 constexpr int BATCH_MAX_THREADS = 128;
+constexpr int BATCH_MIN_BLOCKS = 4;
 template <int S, int KIND, int EQ, int COLL, bool WALLS>
-__global__ void __launch_bounds__(BATCH_MAX_THREADS, 3)
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, BATCH_MIN_BLOCKS)
     k_batch_step(const BatchDesc<typename Storage<S>::C> *__restrict__ descs,
                  const int4 *__restrict__ items, const int *__restrict__ groups,
-                 const long long *__restrict__ g_round, int k) {
+                 const long long *__restrict__ g_round, int k, int slot,
+                 const CollConst<typename Storage<S>::C> kc) {
     using T = typename Storage<S>::T;
     const long long g = *g_round + k;
-    constexpr int combo = ((WALLS ? 1 : 0) * 3 + EQ) * 2 + COLL;
     int lo, hi;
     if constexpr (KIND == BATCH_AB) {
-        lo = groups[combo * 2];
-        hi = groups[combo * 2 + 2];
+        lo = groups[slot * 2];
+        hi = groups[slot * 2 + 2];
     } else {
         const int c = (KIND == BATCH_AA_EVEN) ? (int)(g & 1) : (int)((g & 1) ^ 1);
-        lo = groups[combo * 2 + c];
-        hi = groups[combo * 2 + c + 1];
+        lo = groups[slot * 2 + c];
+        hi = groups[slot * 2 + c + 1];
     }
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
@@ -81,6 +81,8 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 3)
         if (g < d.g_base || g >= d.g_end) continue;  // warp-uniform
         const long long t = d.t_base + (g - d.g_base);
         T *base = static_cast<T *>(d.mem);
+        CollConst<typename Storage<S>::C> kk = kc;
+        kk.lam = d.lam;
         const int rows = 32 >> d.lw;
         for (int q = 0; q < it.w; ++q) {
             const int y0 = it.y + q * rows;
@@ -88,40 +90,48 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 3)
                 const T *src = base + (size_t)(t & 1) * d.buf_elems;
                 T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
                 item_ab<S, EQ, COLL, S == ST_F32, WALLS>(src, dst, d.nx, d.ny, d.pitch, d.plane, y0,
-                                                   it.z, lane, d.lw, d.k, t, d.sr != 0);
+                                                         it.z, lane, d.lw, kk, t, d.sr != 0);
             } else if constexpr (KIND == BATCH_AA_ODD) {
                 item_aa_odd<S, EQ, COLL, S == ST_F32, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
-                                                       it.z, lane, d.lw, d.k, t, d.sr != 0);
+                                                             it.z, lane, d.lw, kk, t, d.sr != 0);
             } else {
-                item_aa_even<S, EQ, COLL, S == ST_F32, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
-                                                        it.z, lane, d.lw, d.k, t, d.sr != 0);
+                item_aa_even<S, EQ, COLL, S == ST_F32, WALLS>(base, d.nx, d.ny, d.pitch, d.plane,
+                                                              y0, it.z, lane, d.lw, kk, t,
+                                                              d.sr != 0);
             }
         }
     }
 }
 
 template <int S> struct BatchLaunchT {
+    using C = typename Storage<S>::C;
+    using D = BatchDesc<C>;
     template <int KIND, bool WALLS, int EQ, int COLL>
-    static void launch_one(const BatchLaunch &a) {
-        constexpr int bit = ((WALLS ? 1 : 0) * 3 + EQ) * 2 + COLL;
-        if (!(a.combos & (1u << bit))) return;
-        using D = BatchDesc<typename Storage<S>::C>;
+    static void launch_one(const BatchLaunch &a, int s) {
+        const CollConst<C> &kc = *static_cast<const CollConst<C> *>(a.slots[s].kconst);
         k_batch_step<S, KIND, EQ, COLL, WALLS><<<a.grid, a.block, 0, a.stream>>>(
-            static_cast<const D *>(a.descs), a.items, a.groups, a.g, a.k);
+            static_cast<const D *>(a.descs), a.items, a.groups, a.g, a.k, s, kc);
+    }
+    template <int KIND, bool WALLS, int EQ>
+    static void launch_coll(const BatchLaunch &a, int s, int coll) {
+        if (coll == COLL_OREG) launch_one<KIND, WALLS, EQ, COLL_OREG>(a, s);
+        else launch_one<KIND, WALLS, EQ, COLL_BGK>(a, s);
     }
     template <int KIND, bool WALLS>
-    static void launch_combos(const BatchLaunch &a) {
-        launch_one<KIND, WALLS, EQ_GUIDED, COLL_OREG>(a);
-        launch_one<KIND, WALLS, EQ_GUIDED, COLL_BGK>(a);
-        launch_one<KIND, WALLS, EQ_POLY2, COLL_OREG>(a);
-        launch_one<KIND, WALLS, EQ_POLY2, COLL_BGK>(a);
-        launch_one<KIND, WALLS, EQ_GUIDED_LOCAL, COLL_OREG>(a);
-        launch_one<KIND, WALLS, EQ_GUIDED_LOCAL, COLL_BGK>(a);
+    static void launch_eq(const BatchLaunch &a, int s, int eq, int coll) {
+        if (eq == EQ_GUIDED) launch_coll<KIND, WALLS, EQ_GUIDED>(a, s, coll);
+        else if (eq == EQ_POLY2) launch_coll<KIND, WALLS, EQ_POLY2>(a, s, coll);
+        else launch_coll<KIND, WALLS, EQ_GUIDED_LOCAL>(a, s, coll);
     }
+    // combo = (walls * 3 + eq) * 2 + coll
     template <int KIND>
     static cudaError_t launch_kind(const BatchLaunch &a) {
-        launch_combos<KIND, false>(a);
-        launch_combos<KIND, true>(a);
+        for (int s = 0; s < a.nslots; ++s) {
+            const int combo = a.slots[s].combo;
+            const int coll = combo & 1, eq = (combo >> 1) % 3, walls = combo / 6;
+            if (walls) launch_eq<KIND, true>(a, s, eq, coll);
+            else launch_eq<KIND, false>(a, s, eq, coll);
+        }
         return cudaGetLastError();
     }
     static cudaError_t launch(const BatchLaunch &a) {
@@ -152,4 +162,5 @@ template <int S> struct BatchLaunchT {
         return BatchLaunchT<S>::occupancy(layout, block);                               \
     }                                                                                   \
     size_t batch_desc_size_##SUFFIX() { return sizeof(BatchDesc<typename Storage<S>::C>); } \
+    size_t batch_const_size_##SUFFIX() { return sizeof(CollConst<typename Storage<S>::C>); } \
     }

@@ -108,19 +108,28 @@ OREG_DECLARE_LAUNCHERS(bf16)
 cudaError_t step_f32c64(const StepArgs &a);
 
 // One launch of the batched stream-collide kernel (see oreg_batch_kernels.cuh).
-// Row groups (32/W rows of one W-lane segment each) per batched work item: a
-// warp takes up to this many consecutive row groups of one lattice segment,
-// reading the lattice's descriptor once.
+// Default row groups (32/W rows of one W-lane segment each) per batched work
+// item: a warp takes up to this many consecutive row groups of one lattice
+// segment, reading the lattice's descriptor once (olb_batch_params.
+// item_row_groups overrides it).
 constexpr int BATCH_ITEM_ROW_GROUPS = 4;
+
+// One slot of a batch: a (walls, equilibrium kind, collision) kernel and the
+// collision constants of one class of lattices (all but 1 - 1/tau).
+struct BatchSlot {
+    int combo;            // (walls * 3 + eq) * 2 + coll
+    const void *kconst;   // host CollConst<C> of the class (copied into the launch)
+};
 
 struct BatchLaunch {
     const void *descs;        // BatchDesc<C>[]
     const int4 *items;        // work items (descriptor, first row, segment), grouped
-    const int *groups;        // device: item offsets of the 24 groups (25 entries)
+    const int *groups;        // device: item offsets of the (slot, parity) groups
     const long long *g;       // device: global step counter of this round
     int k;                    // step within the round
     int layout;
-    unsigned combos;          // kernels to launch: bit ((walls * 3 + eq) * 2 + coll)
+    int nslots;               // slots to launch, one kernel each per step
+    const BatchSlot *slots;
     int grid, block;
     cudaStream_t stream;
 };
@@ -128,7 +137,8 @@ struct BatchLaunch {
 #define OREG_DECLARE_BATCH_LAUNCHERS(SUFFIX)                 \
     cudaError_t batch_step_##SUFFIX(const BatchLaunch &a);   \
     int batch_occupancy_##SUFFIX(int layout, int block);     \
-    size_t batch_desc_size_##SUFFIX();
+    size_t batch_desc_size_##SUFFIX();                       \
+    size_t batch_const_size_##SUFFIX();
 
 OREG_DECLARE_BATCH_LAUNCHERS(f64)
 OREG_DECLARE_BATCH_LAUNCHERS(f32)

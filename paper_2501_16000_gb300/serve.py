@@ -24,7 +24,7 @@ import time
 
 import numpy as np
 
-from .batch import BatchEngine, work_items
+from .batch import ITEM_ROW_GROUPS, BatchEngine, work_items
 from .engine import Lattice, required_bytes
 
 
@@ -76,7 +76,7 @@ def _bytes(lat_case, storage, layout):
 class Server:
     def __init__(self, storage="f16", layout="ab", budget_bytes=120e9, steps_per_launch=100,
                  max_lattices=8192, max_items=1 << 24, warps_per_block=4, blocks_per_sm=0,
-                 keep_fields=True, engine=None):
+                 keep_fields=True, engine=None, item_row_groups=ITEM_ROW_GROUPS):
         """``engine`` replaces the BatchEngine (anything with its new_lattice,
         add, remove, remaining, run, wait and close methods)."""
         self.storage, self.layout = storage, layout
@@ -85,7 +85,8 @@ class Server:
         self.engine = engine if engine is not None else BatchEngine(
             storage, layout, max_lattices=max_lattices, max_items=max_items,
             steps_per_launch=steps_per_launch, warps_per_block=warps_per_block,
-            blocks_per_sm=blocks_per_sm)
+            blocks_per_sm=blocks_per_sm, item_row_groups=item_row_groups)
+        self.item_row_groups = int(item_row_groups)
         self.max_items = max_items
         self.rounds = 0
         self.peak_bytes = 0
@@ -135,13 +136,13 @@ class Server:
                     eng.remove(lat)
                     lat.close()
                     in_bytes -= need
-                    in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage)
+                    in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage, self.item_row_groups)
                     results.append(cancelled(req, adm))
             # FIFO admission against the memory budget (and the item table)
             while queue:
                 req = queue[0]
                 need = _bytes(req.lattice, self.storage, self.layout)
-                items = work_items(req.lattice.nx, req.lattice.ny, self.storage)
+                items = work_items(req.lattice.nx, req.lattice.ny, self.storage, self.item_row_groups)
                 if need > self.budget:
                     raise ValueError(f"request {req.rid} needs {need} B > budget")
                 if in_bytes + need > self.budget or in_items + items > self.max_items:
@@ -172,7 +173,7 @@ class Server:
                 eng.remove(lat)
                 lat.close()
                 in_bytes -= need
-                in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage)
+                in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage, self.item_row_groups)
                 results.append(Result(rid, req.arrival_s * time_scale, adm, now(),
                                       req.lattice.nodes, req.lattice.steps, req.lattice.case,
                                       fields, "ok" if ok else "nonfinite"))

@@ -221,3 +221,41 @@ def test_serving_reports_nonfinite_and_cancelled_requests():
     assert s["nonfinite"] == 1 and s["cancelled"] == len(cancel_at)
     assert s["solves"] == len(trace) - 1 - len(cancel_at)
     assert not eng.left                                        # nothing left in the batch
+
+
+def test_autotune_picks_the_fastest_candidate_and_honours_the_cache(tmp_path):
+    """The tuner with a stand-in measurement (no GPU): a known cost surface,
+    noisy samples whose median is the true cost; it must return the cheapest
+    configuration of its staged search, time each candidate once, take the
+    median of the samples, and answer a second call from the cache."""
+    from paper_2501_16000_gb300 import batch as BT
+    cases = W.batch_mix(8, seed=1)
+    calls = []
+
+    def cost(cfg):
+        c = 1.0
+        c += {"ab": 0.0, "aa": 0.3}[cfg["layout"]]
+        c += {1: 0.2, 2: 0.05, 4: 0.0}[cfg["warps_per_block"]]
+        c += {0: 0.0, 1: 0.4, 2: 0.1}[cfg["blocks_per_sm"]]
+        c += {1: 0.08, 2: 0.0, 4: 0.02, 8: 0.05}[cfg["item_row_groups"]]
+        c += {25: 0.04, 50: 0.02, 100: 0.0, 200: 0.01}[cfg["steps_per_launch"]]
+        return c
+
+    def measure(cfg):
+        calls.append(dict(cfg))
+        c = cost(cfg)
+        return [c + 5.0, c, c - 0.001]        # one outlier: the median is c
+
+    path = str(tmp_path / "tune.json")
+    r = BT.autotune(cases, "f16", repeats=3, cache_path=path, measure=measure)
+    assert (r["layout"], r["warps_per_block"], r["blocks_per_sm"]) == ("ab", 4, 0)
+    assert (r["item_row_groups"], r["steps_per_launch"]) == (2, 100)
+    assert abs(r["ms_per_step"] - 1.0) < 1e-12
+    idents = [tuple(sorted(c.items())) for c in calls]
+    assert len(idents) == len(set(idents)) == r["candidates"]
+    assert {c["steps_per_launch"] for c in calls} == {25, 50, 100, 200}
+    n = len(calls)
+    r2 = BT.autotune(cases, "f16", repeats=3, cache_path=path, measure=measure)
+    assert r2 == r and len(calls) == n                      # answered from the cache
+    r3 = BT.autotune(BT_cases := W.batch_mix(16, seed=1), "f16", cache_path=path, measure=measure)
+    assert len(calls) > n and BT.size_class(BT_cases) != BT.size_class(cases)
