@@ -55,6 +55,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extended", action="store_true",
                     help="skip the batched, serving and precision sections")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched section and print its JSON (profiling)")
+    ap.add_argument("--batch-config", default=None,
+                    help="layout,warps_per_block,blocks_per_sm,item_row_groups,steps_per_launch "
+                         "instead of the autotuner (e.g. ab,2,0,2,100)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--decay-samples", type=int, default=60)
@@ -438,7 +443,12 @@ def batched_section(args):
     cases = W.batch_mix(count=args.batch_count, seed=1, steps=steps)
     nodes = sum(c.nodes for c in cases)
     t_tune = time.perf_counter()
-    tuned = autotune(cases, "f16", use_cache=False)
+    if args.batch_config:
+        lay, w, b, r, k = args.batch_config.split(",")
+        tuned = {"layout": lay, "warps_per_block": int(w), "blocks_per_sm": int(b),
+                 "item_row_groups": int(r), "steps_per_launch": int(k), "given": True}
+    else:
+        tuned = autotune(cases, "f16", use_cache=False)
     t_tune = time.perf_counter() - t_tune
     K, R = tuned["steps_per_launch"], tuned["item_row_groups"]
     items = sum(work_items(c.nx, c.ny, "f16", R) for c in cases)
@@ -493,9 +503,9 @@ def batched_section(args):
                                  "seconds": round(dt_ser, 4),
                                  "mlups": round(nodes * steps / dt_ser / 1e6, 1)},
         "speedup_vs_fp32_serial": round(dt_ser / dt, 2),
-        "decay_rate_error_vs_fp64": {"cases": len(errs), "max": float(f"{errs.max():.3e}"),
-                                     "median": float(f"{np.median(errs):.3e}"),
-                                     "le_1e-4": int((errs <= 1e-4).sum())},
+        "decay_rate_error_vs_fp64": ({"cases": len(errs), "max": float(f"{errs.max():.3e}"),
+                                      "median": float(f"{np.median(errs):.3e}"),
+                                      "le_1e-4": int((errs <= 1e-4).sum())} if len(errs) else None),
     }
 
 
@@ -575,6 +585,11 @@ def lat_bytes(storage, N):
 
 def main():
     args = parse_args()
+    if args.batched_only:
+        from paper_2501_16000_gb300 import build
+        build.build()
+        print(json.dumps(batched_section(args)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -32,6 +32,8 @@ MUTATIONS = [
      "ca = (double)ORA_C[k][a], cb = (double)ORA_C[k][a]"),
     ("absolute instead of peculiar velocity", "C[a] = (double)ORA_C[i][a] - u[a]",
      "C[a] = (double)ORA_C[i][a]"),
+    ("peculiar velocity takes u_x on both axes", "C[a] = (double)ORA_C[i][a] - u[a]",
+     "C[a] = (double)ORA_C[i][a] - u[0]"),
     ("prefactor theta not squared", "(2.0 * rho * theta_eff * theta_eff)",
      "(2.0 * rho * theta_eff)"),
     ("prefactor rho dropped", "(2.0 * rho * theta_eff * theta_eff)",
