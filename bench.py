@@ -511,8 +511,12 @@ def batched_section(args):
 
 def serving_section(args, batched):
     """Serving workload: Poisson arrivals at ~80% of the measured batched capacity,
-    sides 64..2048, steps 100..10000, admission against a 120 GB budget,
-    continuous batching (FP16, stochastic rounding); vs serial FP32 solves."""
+    sides 64..2048, steps 100..10000, continuous batching (FP16, stochastic
+    rounding, the tuned batch configuration), three runs of the same trace:
+    a 120 GB admission budget (not binding), a budget of half that run's peak
+    (binding: requests wait for memory), and every request arriving at once
+    (saturation: the server's own throughput against the batched MLUPS); vs
+    serial FP32 solves of the trace."""
     import numpy as np
     from paper_2501_16000_gb300 import workloads as W
     from paper_2501_16000_gb300.serve import Server, serve_serial, summarize
@@ -521,19 +525,31 @@ def serving_section(args, batched):
     capacity = batched["mlups"] * 1e6 / mean_work            # requests per second
     rate = 0.8 * capacity
     tuned = batched["tuned"]
-    srv = Server("f16", tuned["layout"], budget_bytes=120e9,
-                 steps_per_launch=tuned["steps_per_launch"],
-                 warps_per_block=tuned["warps_per_block"], blocks_per_sm=tuned["blocks_per_sm"],
-                 item_row_groups=tuned["item_row_groups"])
-    res, wall = srv.run(unit, time_scale=1.0 / rate)
-    stats = summarize(res, wall, "continuous batching, FP16 storage")
-    stats.update({"rounds": srv.rounds, "peak_inflight": srv.peak_inflight,
-                  "peak_gb": round(srv.peak_bytes / 1e9, 2)})
-    srv.close()
+
+    def serve(budget, time_scale, label):
+        srv = Server("f16", tuned["layout"], budget_bytes=budget,
+                     steps_per_launch=tuned["steps_per_launch"],
+                     warps_per_block=tuned["warps_per_block"],
+                     blocks_per_sm=tuned["blocks_per_sm"],
+                     item_row_groups=tuned["item_row_groups"])
+        res, wall = srv.run(unit, time_scale=time_scale)
+        stats = summarize(res, wall, label)
+        stats.update({"budget_gb": round(budget / 1e9, 3), "rounds": srv.rounds,
+                      "peak_inflight": srv.peak_inflight,
+                      "peak_gb": round(srv.peak_bytes / 1e9, 3)})
+        srv.close()
+        return stats
+
+    free = serve(120e9, 1.0 / rate, "continuous batching, FP16, 120 GB budget")
+    binding = serve(0.5 * free["peak_gb"] * 1e9, 1.0 / rate,
+                    "continuous batching, FP16, budget = half the unconstrained peak")
+    saturated = serve(120e9, 0.0, "continuous batching, FP16, all requests at t = 0")
+    saturated["vs_batched_mlups"] = round(saturated["mlups"] / batched["mlups"], 3)
     sres, swall = serve_serial(unit, "f32", "ab", time_scale=1.0 / rate)
     return {"requests": len(unit), "rate_per_s": round(rate, 2),
-            "capacity_estimate_per_s": round(capacity, 2), "budget_gb": 120,
-            "served": stats, "baseline_fp32_serial": summarize(sres, swall, "serial FP32")}
+            "capacity_estimate_per_s": round(capacity, 2),
+            "served": free, "served_binding_budget": binding, "served_saturated": saturated,
+            "baseline_fp32_serial": summarize(sres, swall, "serial FP32")}
 
 
 def precision_section(args):

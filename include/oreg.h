@@ -157,14 +157,28 @@ int32_t olb_abi_version(void);
 
 /* Bytes of device memory the populations of a lattice with these
  * parameters occupy (for admission control and caller allocation);
- * 0 if the parameters are invalid.  Library scratch (a few MB at most) is
- * extra and always library-owned. */
+ * 0 if the parameters are invalid.  Library scratch is extra and always
+ * library-owned: ~60 KB of reduction partials per lattice from
+ * olb_create_lattice, and, from the first olb_init_fields / olb_moments /
+ * olb_get_populations / olb_get_region / olb_set_populations call on, an
+ * FP64 staging buffer of at most 128 MiB (for a small lattice 2 x ny x nx
+ * x 3 doubles for fields, ny x nx x 9 for populations), held until
+ * olb_destroy. */
 size_t olb_required_bytes(const olb_params *p);
 
 /* Validates p, allocates the lattice and (unless p->device_buffer is
  * given) its population memory.  The state is undefined until one of the
  * olb_init_* or olb_set_populations calls.  *out receives the handle. */
 olb_status olb_create_lattice(const olb_params *p, olb_lattice **out);
+
+/* Rebinds a lattice to another stream: the work of every later call on it
+ * is enqueued there (a serving loop reads a finished lattice back on its own
+ * stream while the batch's next round runs).  Work already enqueued on the
+ * previous stream is not waited for: the caller orders it, e.g. with an
+ * event.  cuda_stream NULL: back to the stream the library created for the
+ * lattice (OLB_ERR_INVALID if it was created on a caller stream).
+ * OLB_ERR_STATE while the lattice is a batch member. */
+olb_status olb_set_stream(olb_lattice *lat, void *cuda_stream);
 
 /* S_0 = f^eq(rho, u) of a rotated decaying shear wave (Sec. IV, Eq. 18 with
  * any integer wave vector): k = 2 pi (m/nx, n/ny), u = u0 sin(k.x) e_perp,
@@ -300,13 +314,20 @@ typedef struct {
 olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out);
 
 /* Adds an initialised lattice that will advance nsteps more steps over the
- * following rounds.  Waits for the batch's pending rounds.  While a member,
- * the lattice is advanced only by olb_batch_run (olb_step and the init calls
- * return OLB_ERR_STATE); its readback calls may be used between rounds. */
+ * following rounds.  Does not wait for the batch: the change of the device
+ * tables is enqueued on the batch's stream and takes effect from the next
+ * round enqueued after this call (rounds enqueued before it run without the
+ * lattice).  While a member, the lattice is advanced only by olb_batch_run
+ * (olb_step and the init calls return OLB_ERR_STATE); its readback calls may
+ * be used between rounds (they run on the batch's stream). */
 olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps);
 
-/* Removes a member (waits for the batch's pending rounds). olb_destroy of a
- * member removes it first. */
+/* Removes a member, without waiting: rounds enqueued before the call still
+ * advance it (up to its step count), rounds enqueued after it do not.  Its
+ * state is final once those rounds have run (stream order on the batch's
+ * stream, e.g. an event recorded there before olb_set_stream moves the
+ * lattice to another stream).  olb_destroy of a member removes it first and
+ * synchronises the stream before freeing anything. */
 olb_status olb_batch_remove(olb_batch *b, olb_lattice *lat);
 
 /* Enqueues nrounds graph replays of steps_per_launch steps each

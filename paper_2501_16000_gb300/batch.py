@@ -98,7 +98,28 @@ class BatchEngine:
 
     # -- execution ----------------------------------------------------------
     def run(self, nrounds: int = 1) -> None:
+        """Enqueues nrounds graph replays (asynchronous)."""
         B.call("olb_batch_run", self._h, int(nrounds))
+
+    def record_event(self):
+        """A torch CUDA event recorded on the batch's stream after the work
+        enqueued so far (its ``synchronize()`` waits for it)."""
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        return ev
+
+    def side_stream(self):
+        """A new torch stream for work beside the batch's (read-backs)."""
+        import torch
+        return torch.cuda.Stream()
+
+    def read_back(self, lat: Lattice, after, stream, keep_fields: bool = True):
+        """Reads a lattice that left the batch back on `stream` once the
+        batch's work up to the event `after` has run (see
+        ``Lattice.read_back_on``); blocks the calling thread only."""
+        stream.wait_event(after)
+        return lat.read_back_on(stream, keep_fields)
 
     def wait(self) -> None:
         B.call("olb_batch_wait", self._h)

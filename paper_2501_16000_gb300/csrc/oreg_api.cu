@@ -10,6 +10,7 @@
 #include <string>
 
 #include "oreg.h"
+#include "oreg_consts.h"
 #include "oreg_device.cuh"
 #include "oreg_launch.h"
 #include "oreg_lattice.h"
@@ -109,73 +110,6 @@ size_t pop_bytes(const olb_params *p) {
     return (size_t)nbuf * 9 * plane * elem_size(p->storage);
 }
 
-// hi + lo split of a double into the compute type C: hi = (C)v and lo the
-// remainder, so that hi + lo represents v to ~2^-48 in FP32.
-template <typename C>
-void split(double v, C &hi, C &lo) {
-    hi = (C)v;
-    lo = (C)(v - (double)hi);
-}
-
-// Constants of the collision for the compute type C.  The storage shift s_i
-// is the rest equilibrium w_i rho0 rounded to C and corr_i the exact
-// remainder w_i rho0 - s_i; the rest factors and weights are kept as hi + lo
-// pairs (see collide()).
-template <typename C>
-CollConst<C> make_const(const olb_params *p) {
-    CollConst<C> k;
-    const double th = p->eq == OLB_EQ_GUIDED ? p->theta : 1.0 / 3.0;
-    const double psi0[2] = {1.0 - th, 0.5 * th};
-    for (int a = 0; a < 2; ++a) split<C>(psi0[a], k.psi0[a], k.psi0_lo[a]);
-    // classes: rest (psi0 psi0), axis (psi0 psi+-), diagonal (psi+- psi+-)
-    const double w[3] = {psi0[0] * psi0[0], psi0[0] * psi0[1], psi0[1] * psi0[1]};
-    const int count[3] = {1, 4, 4};
-    double corr_sum = 0.0;
-    for (int c = 0; c < 3; ++c) {
-        split<C>(w[c], k.w[c], k.w_lo[c]);
-        const C s = (C)(w[c] * p->rho0);
-        const double corr = w[c] * p->rho0 - (double)s;
-        k.shift[c] = s;
-        k.corr[c] = (C)corr;
-        corr_sum += count[c] * corr;
-    }
-    k.sum_corr = (C)corr_sum;
-    k.rho0 = (C)p->rho0;
-    // split constant of the exact conserved sums: 1.5 * 2^e, 2^e >= 32 rho0
-    k.sigma = (C)(1.5 * std::exp2(std::ceil(std::log2(32.0 * p->rho0))));
-    k.lam = (C)(1.0 - 1.0 / p->tau);
-    k.inv_2th2 = (C)(1.0 / (2.0 * th * th));
-    k.theta = (C)th;
-    return k;
-}
-
-// FP32 constants of the stream-collide kernels, in the storage format's step
-// units (populations, rho0, shifts and corrections times STEP_SCALE, a power
-// of two; see Storage in oreg_device.cuh).
-CollConst<float> make_step_const_f32(const olb_params *p) {
-    olb_params q = *p;
-    if (p->storage == OLB_F16_SHIFTED) q.rho0 *= Storage<ST_F16>::STEP_SCALE;
-    return make_const<float>(&q);
-}
-
-// FP64 constants (initialisation and readback) whose shift is exactly the
-// stored format's shift.
-CollConst<double> make_const_f64_for(const olb_params *p) {
-    CollConst<double> kd = make_const<double>(p);
-    if (p->storage != OLB_F64) {
-        const CollConst<float> kf = make_const<float>(p);
-        const int count[3] = {1, 4, 4};
-        double corr_sum = 0.0;
-        for (int c = 0; c < 3; ++c) {
-            kd.shift[c] = (double)kf.shift[c];
-            kd.corr[c] = kd.w[c] * p->rho0 - kd.shift[c];
-            corr_sum += count[c] * kd.corr[c];
-        }
-        kd.sum_corr = corr_sum;
-    }
-    return kd;
-}
-
 StateGeom geom(const olb_lattice *L) {
     StateGeom g;
     g.nx = L->p.nx;
@@ -265,7 +199,25 @@ olb_status run_init(olb_lattice *L, InitSpec spec) {
     return OLB_OK;
 }
 
+// Reduction partials and the pinned result buffer, allocated on first use (a
+// lattice whose owner never asks for a reduction never allocates them).
+olb_status ensure_reduction(olb_lattice *L) {
+    if (L->d_red) return OLB_OK;
+    OLB_CUDA(cudaMalloc(&L->d_red, ((size_t)RED_BLOCKS_MAX + 1) * RED_QUANTITIES * sizeof(double)),
+             "allocating reduction scratch");
+    cudaError_t e = cudaMallocHost(&L->h_red, RED_QUANTITIES * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(L->d_red);
+        L->d_red = nullptr;
+        L->h_red = nullptr;
+        return cuda_fail(e, "allocating pinned result buffer");
+    }
+    return OLB_OK;
+}
+
 olb_status reduce(olb_lattice *L, const ModeSpec &mode, double out[RED_QUANTITIES]) {
+    olb_status st = ensure_reduction(L);
+    if (st != OLB_OK) return st;
     const StateGeom g = geom(L);
     double *partials = L->d_red;
     double *dres = L->d_red + (size_t)RED_BLOCKS_MAX * RED_QUANTITIES;
@@ -368,11 +320,10 @@ olb_status olb_create_lattice(const olb_params *p, olb_lattice **out) {
     if (e != cudaSuccess) return bail(cuda_fail(e, "querying the device"));
     if (p->cuda_stream) {
         L->stream = static_cast<cudaStream_t>(p->cuda_stream);
-        L->own_stream = false;
     } else {
-        e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
+        e = cudaStreamCreateWithFlags(&L->owned_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return bail(cuda_fail(e, "creating the stream"));
-        L->own_stream = true;
+        L->stream = L->owned_stream;
     }
     if (p->device_buffer) {
         L->mem = p->device_buffer;
@@ -392,17 +343,22 @@ olb_status olb_create_lattice(const olb_params *p, olb_lattice **out) {
     long long blocks = (N + 255) / 256;
     const long long cap = std::min<long long>(RED_BLOCKS_MAX, 8LL * L->num_sms);
     L->red_blocks = (int)std::max<long long>(1, std::min(blocks, cap));
-    e = cudaMalloc(&L->d_red, ((size_t)RED_BLOCKS_MAX + 1) * RED_QUANTITIES * sizeof(double));
-    if (e != cudaSuccess) {
-        L->d_red = nullptr;
-        return bail(cuda_fail(e, "allocating reduction scratch"));
-    }
-    e = cudaMallocHost(&L->h_red, RED_QUANTITIES * sizeof(double));
-    if (e != cudaSuccess) {
-        L->h_red = nullptr;
-        return bail(cuda_fail(e, "allocating pinned result buffer"));
-    }
+    // the reduction scratch is allocated by the first reduction (ensure_reduction)
     *out = L;
+    return OLB_OK;
+}
+
+olb_status olb_set_stream(olb_lattice *L, void *cuda_stream) {
+    if (!L) return fail(OLB_ERR_INVALID, "lattice is NULL");
+    if (L->batch)
+        return fail(OLB_ERR_STATE, "a batch member runs on the batch's stream: remove it first");
+    if (cuda_stream) {
+        L->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (!L->owned_stream)
+            return fail(OLB_ERR_INVALID, "the lattice was created on a caller stream: pass a stream");
+        L->stream = L->owned_stream;
+    }
     return OLB_OK;
 }
 
@@ -797,7 +753,11 @@ olb_status olb_destroy(olb_lattice *L) {
     if (L->d_chunk) cudaFree(L->d_chunk);
     if (L->d_tab) cudaFree(L->d_tab);
     if (L->h_tab) cudaFreeHost(L->h_tab);
-    if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+    if (L->stream != L->owned_stream && L->owned_stream) {
+        cudaError_t e = cudaStreamSynchronize(L->owned_stream);
+        if (e != cudaSuccess && st == OLB_OK) st = cuda_fail(e, "synchronising before destroy");
+    }
+    if (L->owned_stream) cudaStreamDestroy(L->owned_stream);
     delete L;
     return st;
 }

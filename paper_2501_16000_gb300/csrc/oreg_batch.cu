@@ -123,12 +123,22 @@ struct olb_batch {
     int4 *d_items;
     int *d_groups;          // item offsets of the (slot, parity class) groups
     long long *d_g;
+    // Pinned staging of the table uploads, two buffers used alternately: an
+    // upload copies the host tables into one and enqueues its copies on the
+    // batch stream, so joining and leaving never wait for running rounds
+    // (the copies land between rounds in stream order); a buffer is refilled
+    // only after the copies issued from it two uploads earlier have run.
+    char *h_stage[2];
+    size_t stage_bytes[2];
+    cudaEvent_t stage_done[2];
+    bool stage_pending[2];
+    int next_stage;
     // host mirrors
     std::vector<Member> members;
     std::vector<Slot> slots;   // slots in launch order (kept while the graph is valid)
     std::vector<char> h_descs;
     std::vector<int4> h_items;
-    int *h_groups;          // pinned, NGROUPS + 1 entries
+    std::vector<int> h_groups;  // NGROUPS + 1 entries
     long long G;            // global step counter at the start of the next round
     bool captured;
     int graph_slots;        // slots the captured graph launches
@@ -139,6 +149,8 @@ struct olb_batch {
 namespace {
 
 void drop_graph(olb_batch *b) {
+    // replays still queued finish before the executable graph goes away
+    if (b->exec) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
@@ -210,19 +222,37 @@ olb_status upload(olb_batch *b) {
     if ((long long)b->h_items.size() > b->p.max_items)
         return bfail(OLB_ERR_NOMEM, "batch work items %zu exceed max_items %lld", b->h_items.size(),
                      (long long)b->p.max_items);
-    if (nm)
-        B_CUDA(cudaMemcpyAsync(b->d_descs, b->h_descs.data(), b->h_descs.size(),
-                               cudaMemcpyHostToDevice, b->stream),
+    // stage the three tables in one pinned buffer and copy them in stream order
+    const size_t nd = b->h_descs.size(), ni = b->h_items.size() * sizeof(int4),
+                 ng = (NGROUPS + 1) * sizeof(int);
+    const size_t off_i = (nd + 15) / 16 * 16, off_g = off_i + ni, total = off_g + ng;
+    const int s = b->next_stage;
+    if (b->stage_pending[s])
+        B_CUDA(cudaEventSynchronize(b->stage_done[s]), "waiting for an earlier table upload");
+    b->stage_pending[s] = false;
+    if (b->stage_bytes[s] < total) {
+        if (b->h_stage[s]) cudaFreeHost(b->h_stage[s]);
+        b->h_stage[s] = nullptr;
+        b->stage_bytes[s] = 0;
+        const size_t cap = std::max(total, 2 * b->stage_bytes[s ^ 1]);
+        B_CUDA(cudaMallocHost(&b->h_stage[s], cap), "allocating pinned table staging");
+        b->stage_bytes[s] = cap;
+    }
+    char *h = b->h_stage[s];
+    if (nd) std::memcpy(h, b->h_descs.data(), nd);
+    if (ni) std::memcpy(h + off_i, b->h_items.data(), ni);
+    std::memcpy(h + off_g, b->h_groups.data(), ng);
+    if (nd)
+        B_CUDA(cudaMemcpyAsync(b->d_descs, h, nd, cudaMemcpyHostToDevice, b->stream),
                "uploading batch descriptors");
-    if (!b->h_items.empty())
-        B_CUDA(cudaMemcpyAsync(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(int4),
-                               cudaMemcpyHostToDevice, b->stream),
+    if (ni)
+        B_CUDA(cudaMemcpyAsync(b->d_items, h + off_i, ni, cudaMemcpyHostToDevice, b->stream),
                "uploading batch items");
-    B_CUDA(cudaMemcpyAsync(b->d_groups, b->h_groups, (NGROUPS + 1) * sizeof(int), cudaMemcpyHostToDevice,
-                           b->stream),
+    B_CUDA(cudaMemcpyAsync(b->d_groups, h + off_g, ng, cudaMemcpyHostToDevice, b->stream),
            "uploading item groups");
-    // the host vectors may change on the next call
-    B_CUDA(cudaStreamSynchronize(b->stream), "synchronising batch upload");
+    B_CUDA(cudaEventRecord(b->stage_done[s], b->stream), "recording table upload");
+    b->stage_pending[s] = true;
+    b->next_stage = s ^ 1;
     return OLB_OK;
 }
 
@@ -323,9 +353,10 @@ olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out) {
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, (size_t)p->max_items * sizeof(int4));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_groups, (NGROUPS + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_g, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_groups, (NGROUPS + 1) * sizeof(int));
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+        e = cudaEventCreateWithFlags(&b->stage_done[s], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(bcuda(e, "allocating batch tables"));
-    for (int q = 0; q <= NGROUPS; ++q) b->h_groups[q] = 0;
+    b->h_groups.assign(NGROUPS + 1, 0);
     e = cudaMemsetAsync(b->d_g, 0, sizeof(long long), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_groups, 0, (NGROUPS + 1) * sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -352,7 +383,6 @@ olb_status olb_batch_add(olb_batch *b, olb_lattice *lat, int64_t nsteps) {
         return bfail(OLB_ERR_INVALID, "member lattices must be created on the batch's stream");
     if ((int)b->members.size() >= b->p.max_lattices)
         return bfail(OLB_ERR_NOMEM, "batch holds max_lattices = %d lattices", b->p.max_lattices);
-    B_CUDA(cudaStreamSynchronize(b->stream), "waiting for the batch");
     Member m;
     m.lat = lat;
     m.g_base = b->G;
@@ -380,7 +410,6 @@ olb_status olb_batch_remove(olb_batch *b, olb_lattice *lat) {
     auto it = std::find_if(b->members.begin(), b->members.end(),
                            [&](const Member &m) { return m.lat == lat; });
     if (it == b->members.end()) return bfail(OLB_ERR_INVALID, "lattice is not in this batch");
-    B_CUDA(cudaStreamSynchronize(b->stream), "waiting for the batch");
     b->members.erase(it);
     lat->batch = nullptr;
     return upload(b);
@@ -440,7 +469,10 @@ olb_status olb_batch_destroy(olb_batch *b) {
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_groups) cudaFree(b->d_groups);
     if (b->d_g) cudaFree(b->d_g);
-    if (b->h_groups) cudaFreeHost(b->h_groups);
+    for (int s = 0; s < 2; ++s) {
+        if (b->h_stage[s]) cudaFreeHost(b->h_stage[s]);
+        if (b->stage_done[s]) cudaEventDestroy(b->stage_done[s]);
+    }
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return st;

@@ -22,16 +22,16 @@ struct olb_lattice {
     int nbuf;
     void *mem;            // population memory (2 buffers for A-B, 1 for AA)
     bool own_mem;
-    cudaStream_t stream;
-    bool own_stream;
+    cudaStream_t stream;        // stream of every call on the lattice (olb_set_stream)
+    cudaStream_t owned_stream;  // stream the library created for it, or NULL
     int64_t t;            // time of the canonical state; -1 = uninitialised
     int comp;
     int sr;               // stochastic rounding of half formats
     int f64_coll;         // FP32 storage: collision in FP64 (OLB_OPT_F64_COLLISION)
     int warps_per_block;
     int num_sms;
-    double *d_red;        // reduction partials + result (library scratch)
-    double *h_red;        // pinned host copy of the result
+    double *d_red;        // reduction partials + result (library scratch, lazy)
+    double *h_red;        // pinned host copy of the result (lazy)
     int red_blocks;
     void *d_chunk;        // readback scratch (lazy)
     size_t chunk_bytes;

@@ -21,6 +21,7 @@
 
 #include "oreg.h"
 #include "oreg_aux.cuh"
+#include "oreg_consts.h"
 
 namespace oreg {
 void set_last_error_message(const char *msg);
@@ -121,31 +122,6 @@ __global__ void __launch_bounds__(NOALLOC_THREADS)
     }
 }
 
-// Storage shift and equilibrium constants as liboreg uses them for a lattice
-// with these parameters (the shift in the stored format's compute precision).
-CollConst<double> noalloc_constants(const olb_params *p) {
-    CollConst<double> k{};
-    const double th = p->eq == OLB_EQ_GUIDED ? p->theta : 1.0 / 3.0;
-    const double psi0[2] = {1.0 - th, 0.5 * th};
-    for (int a = 0; a < 2; ++a) k.psi0[a] = psi0[a];
-    const double w[3] = {psi0[0] * psi0[0], psi0[0] * psi0[1], psi0[1] * psi0[1]};
-    const int count[3] = {1, 4, 4};
-    double corr_sum = 0.0;
-    for (int c = 0; c < 3; ++c) {
-        const double s = p->storage == OLB_F64 ? w[c] * p->rho0 : (double)(float)(w[c] * p->rho0);
-        k.w[c] = w[c];
-        k.shift[c] = s;
-        k.corr[c] = w[c] * p->rho0 - s;
-        corr_sum += count[c] * k.corr[c];
-    }
-    k.sum_corr = corr_sum;
-    k.rho0 = p->rho0;
-    k.lam = 1.0 - 1.0 / p->tau;
-    k.inv_2th2 = 1.0 / (2.0 * th * th);
-    k.theta = th;
-    return k;
-}
-
 template <int S>
 cudaError_t launch_rows(const void *base, const StateGeom &g, const CollConst<double> &kd,
                         double *partials, double *out, cudaStream_t s) {
@@ -221,7 +197,9 @@ extern "C" olb_status olb_diagnostics_noalloc(const void *d_populations, const o
     } else {
         g.mode = (t & 1) ? STATE_AA_ODD : STATE_AA_EVEN;
     }
-    const CollConst<double> kd = noalloc_constants(p);
+    // the FP64 constants liboreg uses for a lattice with these parameters
+    // (shifts exactly those of the stored format)
+    const CollConst<double> kd = make_const_f64_for(p);
     cudaStream_t s = static_cast<cudaStream_t>(p->cuda_stream);
     switch (p->storage) {
         case OLB_F64: e = launch_rows<ST_F64>(base, g, kd, partials, d_out, s); break;

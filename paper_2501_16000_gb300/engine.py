@@ -131,6 +131,50 @@ class Lattice:
     def set_option(self, option: int, value: int) -> None:
         B.call("olb_set_option", self.handle, int(option), int(value))
 
+    def set_stream(self, stream) -> None:
+        """Runs every later call of this lattice on the torch stream `stream`
+        (olb_set_stream); the caller orders it after work already enqueued."""
+        B.call("olb_set_stream", self.handle, ctypes.c_void_p(stream.cuda_stream))
+        self.stream = stream
+
+    def read_back_on(self, stream, keep_fields: bool = True):
+        """Reads the state back on `stream` without the library allocating
+        device memory: the FP64 diagnostics through olb_diagnostics_noalloc
+        (its fixed scratch; callers must not overlap such calls on the GPU)
+        and, if asked, rho and u through olb_moments_device into torch
+        buffers copied to pinned host memory.  The lattice moves to `stream`;
+        the caller orders `stream` after the lattice's last update.  Blocks
+        until `stream` has run the readback.  Returns (mass, non-finite node
+        count, (rho, ux, uy) or None); the fields are None for a state with
+        non-finite nodes."""
+        import torch
+        if self._buf is None:
+            raise RuntimeError("read_back_on needs torch memory")
+        self.set_stream(stream)
+        with torch.cuda.stream(stream):
+            d_out = torch.empty(4, dtype=torch.float64, device="cuda")
+            p = B.olb_params.from_buffer_copy(self.params)
+            p.cuda_stream = stream.cuda_stream
+            B.call("olb_diagnostics_noalloc", ctypes.c_void_p(self._buf.data_ptr()),
+                   ctypes.byref(p), self.time, ctypes.c_void_p(d_out.data_ptr()))
+            h_out = torch.empty(4, dtype=torch.float64, pin_memory=True)
+            h_out.copy_(d_out, non_blocking=True)
+            h = None
+            if keep_fields:
+                d = torch.empty((3, self.ny, self.nx), dtype=torch.float64, device="cuda")
+                B.call("olb_moments_device", self.handle, ctypes.c_void_p(d[0].data_ptr()),
+                       ctypes.c_void_p(d[1].data_ptr()), ctypes.c_void_p(d[2].data_ptr()), None)
+                h = torch.empty((3, self.ny, self.nx), dtype=torch.float64, pin_memory=True)
+                h.copy_(d, non_blocking=True)
+        stream.synchronize()
+        out = h_out.numpy()
+        nonfinite = int(round(out[3]))
+        fields = None
+        if h is not None and nonfinite == 0:
+            a = h.numpy()
+            fields = (a[0].copy(), a[1].copy(), a[2].copy())
+        return float(out[0]), nonfinite, fields
+
     def init_shear_wave(self, rho0=1.0, u0=0.05, m=1, n=0) -> None:
         B.call("olb_init_shear_wave", self.handle, float(rho0), float(u0), int(m), int(n))
 

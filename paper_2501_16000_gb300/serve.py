@@ -2,16 +2,24 @@
 
 Requests (``workloads.Request``: arrival time, lattice, step count) arrive
 over wall-clock time.  Arrived requests wait in a FIFO queue and are admitted
-as soon as their population memory (``olb_required_bytes``) fits the HBM
-budget next to everything in flight; admitted requests join the running
-``BatchEngine`` and advance together with all other in-flight requests, one
-CUDA-graph round of K steps at a time, their states resident in HBM.  A
-request whose steps are done is checked (FP64 diagnostics: a solve that turned
-non-finite is reported with status "nonfinite" and no fields), read back
-(moments to host), removed and its memory freed, which may admit the next
-ones.  A request can be cancelled while it waits or while it runs (status
-"cancelled"; an in-flight one leaves the batch at the next round boundary and
-frees its memory).  Latency is arrival -> result in host memory.
+as soon as their device memory (``Server.request_bytes``: populations plus the
+FP64 fields they are read back into) fits the HBM budget next to everything
+in flight; admitted requests join the running ``BatchEngine`` and advance
+together with all other in-flight requests, one CUDA-graph round of K steps
+at a time, their states resident in HBM.  A request whose steps are done
+leaves the batch and is read back on a side stream by a worker thread (FP64
+diagnostics: a solve that turned non-finite is reported with status
+"nonfinite" and no fields; moments to host), after which its memory is freed,
+which may admit the next ones.  A request can be cancelled while it waits or
+while it runs (status "cancelled"; an in-flight one leaves the batch at the
+next round boundary and frees its memory).  Latency is arrival -> result in
+host memory.
+
+The loop keeps the GPU fed: joining and leaving the batch enqueue their table
+changes on the batch's stream without waiting, round r + 1 is enqueued before
+the host waits for round r, and the read-back of requests that finished in a
+round runs on its own stream, overlapping the next round, while the host
+admits new requests.  The library allocates no device memory on this path.
 
 ``serve_serial`` replays the same trace with one plain FP32 single-lattice
 solve at a time (the baseline).
@@ -19,6 +27,7 @@ solve at a time (the baseline).
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
 import time
 
@@ -78,7 +87,8 @@ class Server:
                  max_lattices=8192, max_items=1 << 24, warps_per_block=4, blocks_per_sm=0,
                  keep_fields=True, engine=None, item_row_groups=ITEM_ROW_GROUPS):
         """``engine`` replaces the BatchEngine (anything with its new_lattice,
-        add, remove, remaining, run, wait and close methods)."""
+        add, remove, remaining, run, record_event, read_back and close
+        methods)."""
         self.storage, self.layout = storage, layout
         self.budget = float(budget_bytes)
         self.keep_fields = keep_fields
@@ -95,6 +105,12 @@ class Server:
     def close(self):
         self.engine.close()
 
+    def request_bytes(self, case) -> int:
+        """Device memory a request holds while admitted: its populations and,
+        when fields are kept, the FP64 rho, u_x, u_y it is read back into."""
+        fields = 24 * case.nodes + 64 if self.keep_fields else 64
+        return _bytes(case, self.storage, self.layout) + fields
+
     def run(self, trace, time_scale: float = 1.0, cancel_at=None, prepare=None):
         """Serves the trace in real time (arrival times scaled by time_scale);
         returns (results, wall seconds).
@@ -106,11 +122,14 @@ class Server:
         eng = self.engine
         pending = collections.deque(sorted(trace, key=lambda r: r.arrival_s))
         queue = collections.deque()
-        inflight = {}           # rid -> (request, lattice, bytes, admitted_s)
+        inflight = {}           # rid -> (request, lattice, bytes, items, admitted_s)
+        finishing = {}          # rid -> future of (Result, bytes, items)
+        rounds = collections.deque()   # events of enqueued rounds not yet waited for
         in_bytes = 0
         in_items = 0
         results = []
         cancels = dict(cancel_at or {})
+        side = eng.side_stream() if hasattr(eng, "side_stream") else None
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
 
@@ -119,64 +138,88 @@ class Server:
                           req.lattice.nodes, req.lattice.steps, req.lattice.case, None,
                           "cancelled")
 
-        while pending or queue or inflight:
-            t = now()
-            while pending and pending[0].arrival_s * time_scale <= t:
-                queue.append(pending.popleft())
-            # cancellations that are due: drop waiting requests, evict running ones
-            for rid in [r for r, ct in cancels.items() if ct * time_scale <= t]:
-                del cancels[rid]
-                for dq in (pending, queue):
-                    hit = [q for q in dq if q.rid == rid]
-                    for q in hit:
-                        dq.remove(q)
-                        results.append(cancelled(q, now()))
-                if rid in inflight:
-                    req, lat, need, adm = inflight.pop(rid)
-                    eng.remove(lat)
-                    lat.close()
+        def finish(req, lat, after, need, items, adm):
+            # worker thread: waits for the round, reads back, frees the lattice
+            _, nonfinite, fields = eng.read_back(lat, after, side, self.keep_fields)
+            lat.close()
+            ok = nonfinite == 0
+            res = Result(req.rid, req.arrival_s * time_scale, adm, now(), req.lattice.nodes,
+                         req.lattice.steps, req.lattice.case, fields if ok else None,
+                         "ok" if ok else "nonfinite")
+            return res, need, items
+
+        worker = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+        try:
+            while pending or queue or inflight or finishing:
+                # read-backs that completed free their memory for admission
+                for rid in [r for r, fut in finishing.items() if fut.done()]:
+                    res, need, items = finishing.pop(rid).result()
+                    results.append(res)
                     in_bytes -= need
-                    in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage, self.item_row_groups)
-                    results.append(cancelled(req, adm))
-            # FIFO admission against the memory budget (and the item table)
-            while queue:
-                req = queue[0]
-                need = _bytes(req.lattice, self.storage, self.layout)
-                items = work_items(req.lattice.nx, req.lattice.ny, self.storage, self.item_row_groups)
-                if need > self.budget:
-                    raise ValueError(f"request {req.rid} needs {need} B > budget")
-                if in_bytes + need > self.budget or in_items + items > self.max_items:
-                    break
-                queue.popleft()
-                lat = eng.new_lattice(req.lattice)
-                if prepare is not None:
-                    prepare(req, lat)
-                eng.add(lat, req.lattice.steps)
-                inflight[req.rid] = (req, lat, need, now())
-                in_bytes += need
-                in_items += items
-            self.peak_bytes = max(self.peak_bytes, in_bytes)
-            self.peak_inflight = max(self.peak_inflight, len(inflight))
-            if not inflight:
+                    in_items -= items
+                t = now()
+                while pending and pending[0].arrival_s * time_scale <= t:
+                    queue.append(pending.popleft())
+                # cancellations that are due: drop waiting requests, evict running ones
+                for rid in [r for r, ct in cancels.items() if ct * time_scale <= t]:
+                    del cancels[rid]
+                    for dq in (pending, queue):
+                        hit = [q for q in dq if q.rid == rid]
+                        for q in hit:
+                            dq.remove(q)
+                            results.append(cancelled(q, now()))
+                    if rid in inflight:
+                        req, lat, need, items, adm = inflight.pop(rid)
+                        eng.remove(lat)
+                        lat.close()     # waits for the rounds already enqueued
+                        in_bytes -= need
+                        in_items -= items
+                        results.append(cancelled(req, adm))
+                # FIFO admission against the memory budget (and the item table)
+                while queue:
+                    req = queue[0]
+                    need = self.request_bytes(req.lattice)
+                    items = work_items(req.lattice.nx, req.lattice.ny, self.storage,
+                                       self.item_row_groups)
+                    if need > self.budget:
+                        raise ValueError(f"request {req.rid} needs {need} B > budget")
+                    if in_bytes + need > self.budget or in_items + items > self.max_items:
+                        break
+                    queue.popleft()
+                    lat = eng.new_lattice(req.lattice)
+                    if prepare is not None:
+                        prepare(req, lat)
+                    eng.add(lat, req.lattice.steps)
+                    inflight[req.rid] = (req, lat, need, items, now())
+                    in_bytes += need
+                    in_items += items
+                self.peak_bytes = max(self.peak_bytes, in_bytes)
+                self.peak_inflight = max(self.peak_inflight, len(inflight) + len(finishing))
+                if inflight:
+                    eng.run(1)
+                    self.rounds += 1
+                    ev = eng.record_event()
+                    for rid in [r for r, v in inflight.items() if eng.remaining(v[1]) == 0]:
+                        req, lat, need, items, adm = inflight.pop(rid)
+                        eng.remove(lat)
+                        finishing[rid] = worker.submit(finish, req, lat, ev, need, items, adm)
+                    # round r + 1 is enqueued before the host waits for round r
+                    rounds.append(ev)
+                    if len(rounds) > 1:
+                        rounds.popleft().synchronize()
+                    continue
+                while rounds:
+                    rounds.popleft().synchronize()
+                # idle: wait for the next arrival or a read-back
+                wait = 0.01
                 if pending:
-                    wait = pending[0].arrival_s * time_scale - now()
-                    if wait > 0:
-                        time.sleep(min(wait, 0.01))
-                continue
-            eng.run(1)
-            eng.wait()
-            self.rounds += 1
-            for rid in [r for r, (_, lat, _, _) in inflight.items() if eng.remaining(lat) == 0]:
-                req, lat, need, adm = inflight.pop(rid)
-                ok = lat.diagnostics(raise_nonfinite=False)["nonfinite"] == 0
-                fields = lat.moments() if self.keep_fields and ok else None
-                eng.remove(lat)
-                lat.close()
-                in_bytes -= need
-                in_items -= work_items(req.lattice.nx, req.lattice.ny, self.storage, self.item_row_groups)
-                results.append(Result(rid, req.arrival_s * time_scale, adm, now(),
-                                      req.lattice.nodes, req.lattice.steps, req.lattice.case,
-                                      fields, "ok" if ok else "nonfinite"))
+                    wait = min(wait, pending[0].arrival_s * time_scale - now())
+                if finishing:
+                    wait = min(wait, 0.0005)
+                if wait > 0:
+                    time.sleep(wait)
+        finally:
+            worker.shutdown(wait=True)
         return results, now()
 
 

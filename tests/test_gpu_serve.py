@@ -46,17 +46,16 @@ def test_served_results_equal_alone(layout):
 
 
 def test_admission_respects_the_budget():
-    from paper_2501_16000_gb300.engine import required_bytes
     from paper_2501_16000_gb300.serve import Server
     trace = small_trace(n=10, seed=3)
-    sizes = [required_bytes(nx=r.lattice.nx, ny=r.lattice.ny, tau=r.lattice.tau,
-                            storage="f16", layout="ab") for r in trace]
-    budget = 2 * max(sizes)
-    srv = Server("f16", "ab", budget_bytes=budget, steps_per_launch=16)
+    srv = Server("f16", "ab", budget_bytes=1.0, steps_per_launch=16)
+    sizes = [srv.request_bytes(r.lattice) for r in trace]
+    srv.budget = budget = 2 * max(sizes)
     results, _ = srv.run(trace)
     srv.close()
     assert len(results) == len(trace)
     assert srv.peak_bytes <= budget
+    assert srv.peak_bytes > max(sizes)       # requests did overlap within the budget
 
 
 def test_nonfinite_request_is_reported_and_the_others_are_unaffected():

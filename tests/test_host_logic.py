@@ -121,7 +121,20 @@ class _FakeEngine:
     def wait(self):
         pass
 
+    def record_event(self):
+        return _Done()
+
+    def read_back(self, lat, after, stream, keep_fields=True):
+        after.synchronize()
+        d = lat.diagnostics(raise_nonfinite=False)
+        return d["mass"], d["nonfinite"], (lat.moments() if keep_fields else None)
+
     def close(self):
+        pass
+
+
+class _Done:
+    def synchronize(self):
         pass
 
 
@@ -131,8 +144,10 @@ def test_serving_admission_fifo_and_budget():
     from paper_2501_16000_gb300.serve import Server
     trace = W.arrival_trace(30, rate_per_s=2000.0, seed=5, lo=16, hi=256, steps_lo=10,
                             steps_hi=500)
-    sizes = [required_bytes(nx=r.lattice.nx, ny=r.lattice.ny, tau=r.lattice.tau,
-                            storage="f16", layout="ab") for r in trace]
+    probe = Server("f16", "ab", engine=_FakeEngine(K=1))
+    sizes = [probe.request_bytes(r.lattice) for r in trace]
+    assert all(sz > required_bytes(nx=r.lattice.nx, ny=r.lattice.ny, tau=r.lattice.tau,
+                                   storage="f16", layout="ab") for sz, r in zip(sizes, trace))
     budget = 3 * max(sizes)
     eng = _FakeEngine(K=50)
     srv = Server("f16", "ab", budget_bytes=budget, engine=eng)
@@ -200,8 +215,8 @@ def test_serving_reports_nonfinite_and_cancelled_requests():
     long_run = max(trace, key=lambda r: r.lattice.steps)      # cancelled while running
     early = next(r.rid for r in reversed(by_arrival) if r.rid != long_run.rid)  # before arrival
     poison = next(r.rid for r in by_arrival if r.rid not in (long_run.rid, early))
-    sizes = [required_bytes(nx=r.lattice.nx, ny=r.lattice.ny, tau=r.lattice.tau,
-                            storage="f16", layout="ab") for r in trace]
+    sizes = [Server("f16", "ab", engine=_FakeEngine(K=1)).request_bytes(r.lattice)
+             for r in trace]
     eng = _FakeEngine(K=50, round_s=0.002)
     srv = Server("f16", "ab", budget_bytes=sum(sizes), engine=eng)
     cancel_at = {early: -1.0, long_run.rid: long_run.arrival_s + 0.006}

@@ -50,28 +50,47 @@ def _check(got, want):
     assert int(round(got[3])) == want["nonfinite"]
 
 
-def test_noalloc_matches_diagnostics_on_two_calls_in_a_row(lib):
+def _two_calls(lib, storage, layout, t1, t2, **kw):
+    """Call 1 on a taller lattice (150 rows) leaves row partials that call 2,
+    on a shorter one (23 rows, one planted non-finite node), must not pick
+    up; both against olb_diagnostics of the same state."""
     import torch
 
     from paper_2501_16000_gb300.engine import Lattice
 
     d_out = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
-    # call 1: a taller lattice (FP32, A-B, odd time) leaves 150 row partials
-    with Lattice(200, 150, 0.6, storage="f32", layout="ab", torch_memory=True) as a:
+    with Lattice(200, 150, 0.6, storage=storage, layout=layout, torch_memory=True, **kw) as a:
         a.init_shear_wave(1.0, 0.05, 2, 3)
-        a.step(7)
+        a.step(t1)
         _check(_noalloc(lib, a, d_out), a.diagnostics())
-    # call 2: a shorter lattice (FP64, in-place AA, even time, one non-finite
-    # node); the array still holds the first call's partials beyond row 23
-    with Lattice(37, 23, 0.51, storage="f64", layout="aa", torch_memory=True) as b:
+    with Lattice(37, 23, 0.51, storage=storage, layout=layout, torch_memory=True, **kw) as b:
         b.init_shock_tube(1.5, 0.75, 18)
-        b.step(4)
+        b.step(t2)
         f = b.populations()
-        f[5, 11, 36] = np.nan
+        f[5, 11, 30] = np.nan
         b.set_populations(f, b.time)
         want = b.diagnostics(raise_nonfinite=False)
         assert want["nonfinite"] == 1
         _check(_noalloc(lib, b, d_out), want)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+def test_noalloc_matches_diagnostics_on_two_calls_in_a_row(lib, storage, layout):
+    """Every storage format (FP16 stored as g * 2^8 and decoded with its
+    scale; BF16 unscaled) and both layouts, one call at an odd and one at an
+    even time (the A-B buffer and the AA parity each take both values)."""
+    _two_calls(lib, storage, layout, 7, 4)
+    _two_calls(lib, storage, layout, 4, 7)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_noalloc_on_wall_and_local_temperature_lattices(lib, layout):
+    """Lattices with bounce-back wall columns and with the local-temperature
+    guided equilibrium hold their state in the same layout; the reduction
+    reads it the same way."""
+    _two_calls(lib, "f16", layout, 5, 6, boundary="walls_x")
+    _two_calls(lib, "f32", layout, 6, 5, theta_mode="local")
 
 
 def test_noalloc_rejects_more_rows_than_its_scratch_holds(lib):
