@@ -62,7 +62,8 @@ def parse_args():
                          "instead of the autotuner (e.g. ab,2,0,2,100)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=1000)
-    ap.add_argument("--decay-samples", type=int, default=60)
+    ap.add_argument("--decay-samples", type=int, default=1000,
+                    help="shear lattices of the batched mix whose decay-rate error is measured")
     ap.add_argument("--serve-count", type=int, default=300)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-side", type=int, default=1024)
@@ -428,16 +429,61 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
+def _timed_batch_solve(groups, tuned, steps):
+    """Wall seconds of one solve of `steps` steps of every lattice, the cases
+    of each storage format in its own BatchEngine (own stream), the engines'
+    rounds enqueued side by side; a warm-up solve (graph capture) first, and
+    states created and initialised outside the timed region."""
+    import torch
+    from paper_2501_16000_gb300.batch import BatchEngine, work_items
+    K, R = tuned["steps_per_launch"], tuned["item_row_groups"]
+    engines = []
+    for storage, cases in groups.items():
+        if cases:
+            items = sum(work_items(c.nx, c.ny, storage, R) for c in cases)
+            engines.append((BatchEngine(storage, tuned["layout"], max_lattices=len(cases),
+                                        max_items=items, steps_per_launch=K,
+                                        warps_per_block=tuned["warps_per_block"],
+                                        blocks_per_sm=tuned["blocks_per_sm"],
+                                        item_row_groups=R), cases))
+    try:
+        for rep in range(2):
+            lats = []
+            for eng, cases in engines:
+                for c in cases:
+                    lat = eng.new_lattice(c)
+                    eng.add(lat, steps)
+                    lats.append(lat)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range((steps + K - 1) // K):
+                for eng, _ in engines:
+                    eng.run(1)
+            for eng, _ in engines:
+                eng.wait()
+            dt = time.perf_counter() - t0
+            for lat in lats:
+                lat.close()
+    finally:
+        for eng, _ in engines:
+            eng.close()
+    return dt
+
+
 def batched_section(args):
-    """Batched workload: 512 independent uneven lattices, FP16 storage (stochastic
-    rounding) / FP32 compute, autotuned batch (layout, block shape, grid, row
-    groups per work item, steps per CUDA-graph replay); against serial plain
-    FP32 single-lattice solves of the same set."""
+    """Batched workload: 512 independent uneven lattices (shear waves and shock
+    tubes), FP16 storage (stochastic rounding) / FP32 compute, autotuned batch
+    (layout, block shape, grid, row groups per work item, steps per CUDA-graph
+    replay).  Timed twice: every lattice in FP16, and with precision routing
+    (shear waves whose decay rate FP16 cannot resolve to 1e-4 run in an FP32
+    batch beside the FP16 one); against serial plain FP32 single-lattice
+    solves of the same set.  Decay-rate error against FP64 for every shear
+    lattice of the mix, in FP16 and in the routed format."""
     import numpy as np
     import torch
     from paper_2501_16000_gb300 import workloads as W
     from paper_2501_16000_gb300.analysis import measure_decay
-    from paper_2501_16000_gb300.batch import BatchEngine, autotune, work_items
+    from paper_2501_16000_gb300.batch import autotune, route_storage
     from paper_2501_16000_gb300.engine import Lattice
     steps = args.batch_steps
     cases = W.batch_mix(count=args.batch_count, seed=1, steps=steps)
@@ -450,23 +496,12 @@ def batched_section(args):
     else:
         tuned = autotune(cases, "f16", use_cache=False)
     t_tune = time.perf_counter() - t_tune
-    K, R = tuned["steps_per_launch"], tuned["item_row_groups"]
-    items = sum(work_items(c.nx, c.ny, "f16", R) for c in cases)
-    with BatchEngine("f16", tuned["layout"], max_lattices=len(cases), max_items=items,
-                     steps_per_launch=K, warps_per_block=tuned["warps_per_block"],
-                     blocks_per_sm=tuned["blocks_per_sm"], item_row_groups=R) as eng:
-        # warm-up solve (graph capture), then the timed solve on fresh states
-        for rep in range(2):
-            lats = [eng.new_lattice(c) for c in cases]
-            for lat in lats:
-                eng.add(lat, steps)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            eng.run((steps + K - 1) // K)
-            eng.wait()
-            dt = time.perf_counter() - t0
-            for lat in lats:
-                lat.close()
+    K = tuned["steps_per_launch"]
+    dt = _timed_batch_solve({"f16": cases}, tuned, steps)
+    route = [route_storage(c, "f16") for c in cases]
+    routed = {"f16": [c for c, r in zip(cases, route) if r == "f16"],
+              "f32": [c for c, r in zip(cases, route) if r == "f32"]}
+    dt_routed = _timed_batch_solve(routed, tuned, steps)
     # serial plain FP32: the same lattices one after another (states created
     # and initialised outside the timed region, as for the batch)
     ser = [Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, "f32", "ab") for c in cases]
@@ -481,17 +516,27 @@ def batched_section(args):
     dt_ser = time.perf_counter() - t0
     for lat in ser:
         lat.close()
-    # decay-rate error of F16 (stochastic rounding) vs FP64 on shear lattices of the mix
+    # decay-rate error against FP64 of the shear lattices of the mix (single-
+    # lattice runs: batched results are bitwise those of the lattice alone)
     shear = [c for c in cases if c.case == "shear"][: args.decay_samples]
-    errs = []
+    err16, err_routed = [], []
     for c in shear:
         g = {}
-        for st in ("f64", "f16"):
+        for st in ("f64", "f16", "f32") if route_storage(c, "f16") == "f32" else ("f64", "f16"):
             with Lattice(c.nx, c.ny, c.tau, c.theta, storage=st, layout="ab") as lat:
                 lat.init_case(c)
                 g[st] = measure_decay(lat, c, steps, every=20)[0]
-        errs.append(abs(g["f16"] / g["f64"] - 1))
-    errs = np.array(errs)
+        err16.append(abs(g["f16"] / g["f64"] - 1))
+        err_routed.append(abs(g[route_storage(c, "f16")] / g["f64"] - 1))
+
+    def stats(e):
+        e = np.array(e)
+        if not len(e):
+            return None
+        return {"cases": len(e), "max": float(f"{e.max():.3e}"),
+                "median": float(f"{np.median(e):.3e}"), "le_1e-4": int((e <= 1e-4).sum())}
+
+    r32 = routed["f32"]
     return {
         "workload": f"{len(cases)} lattices, sides log-uniform [32,1024] (seed 1), tau U[0.51,1], "
                     f"u0 U[0.01,0.1], shear/shock 50/50, {steps} steps each, FP16 storage "
@@ -499,13 +544,19 @@ def batched_section(args):
         "nodes": nodes, "solves_per_s": round(len(cases) / dt, 2), "seconds": round(dt, 4),
         "mlups": round(nodes * steps / dt / 1e6, 1), "tuned": tuned,
         "tune_seconds": round(t_tune, 1),
+        "routed": {"rule": "shear waves with 1/(u0 sqrt(N) gamma T) > 0.12 in FP32 storage",
+                   "fp32_lattices": len(r32),
+                   "fp32_node_fraction": round(sum(c.nodes for c in r32) / nodes, 4),
+                   "solves_per_s": round(len(cases) / dt_routed, 2),
+                   "seconds": round(dt_routed, 4),
+                   "mlups": round(nodes * steps / dt_routed / 1e6, 1),
+                   "speedup_vs_fp32_serial": round(dt_ser / dt_routed, 2),
+                   "decay_rate_error_vs_fp64": stats(err_routed)},
         "baseline_fp32_serial": {"solves_per_s": round(len(cases) / dt_ser, 2),
                                  "seconds": round(dt_ser, 4),
                                  "mlups": round(nodes * steps / dt_ser / 1e6, 1)},
         "speedup_vs_fp32_serial": round(dt_ser / dt, 2),
-        "decay_rate_error_vs_fp64": ({"cases": len(errs), "max": float(f"{errs.max():.3e}"),
-                                      "median": float(f"{np.median(errs):.3e}"),
-                                      "le_1e-4": int((errs <= 1e-4).sum())} if len(errs) else None),
+        "decay_rate_error_vs_fp64": stats(err16),
     }
 
 

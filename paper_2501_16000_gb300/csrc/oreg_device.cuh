@@ -388,9 +388,23 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         pxy = (g[5] + g[7]) - (g[6] + g[8]);
         if constexpr (LOCAL) tg = ((g[1] + g[3]) + (g[2] + g[4])) + C(2) * ((g[5] + g[7]) + (g[6] + g[8]));
     }
+    // Scalar FP32 (UNBIASED): no rounding that repeats identically at every
+    // node may enter the update.  rho = rho0 + drho rounds to the same float
+    // wherever rho is near rho0, and so does 1/rho: products with the rounded
+    // rho or 1/rho carry a relative error of up to 2^-24 that is the same
+    // everywhere, a per-step bias of ~1e-8 that a slowly decaying shear wave
+    // (decay ~1e-5 per step) turns into a decay-rate error of 1e-4..4e-4.  So
+    // rho enters products as rho0 x + drho x, and 1/rho carries the residual
+    // of its rounding against rho0 + drho.
+    constexpr bool UNBIASED = std::is_same<C, float>::value;
     const C rho = k.rho0 + drho;
     const C inv_rho = C(1) / rho;
-    const C ux = jx * inv_rho, uy = jy * inv_rho;
+    C inv_lo = C(0);
+    if constexpr (UNBIASED)
+        inv_lo = fma(-drho, inv_rho, fma(-k.rho0, inv_rho, C(1))) * inv_rho;
+    auto rho_times = [&](C x) { return UNBIASED ? fma(drho, x, k.rho0 * x) : rho * x; };
+    const C ux = UNBIASED ? fma(jx, inv_rho, jx * inv_lo) : jx * inv_rho;
+    const C uy = UNBIASED ? fma(jy, inv_rho, jy * inv_lo) : jy * inv_rho;
     const C ux2 = ux * ux, uy2 = uy * uy;
     // Local temperature (EQ_GUIDED_LOCAL): 2 rho theta = <f,c^2> - rho u^2
     // (Eq. 2a energy), written as theta = theta_ref + dth with
@@ -425,6 +439,15 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         C c3[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) c3[c] = PACKED ? fma(drho, k.w_lo[c], k.corr[c]) : k.corr[c];
+        // UNBIASED: the shift correction corr (below half a unit of geq) is
+        // added inside the sum that forms t, as corr / rho, so that it is
+        // rounded together with the exact value; added to the already
+        // rounded rho t it would be rounded away alike at every node.
+        C cr[3] = {C(0), C(0), C(0)};
+        if constexpr (UNBIASED) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cr[c] = k.corr[c] * (inv_rho + inv_lo);
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int a = kidx(cx_of(i)), b = kidx(cy_of(i));
@@ -432,11 +455,14 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
             // dPsi_a Psi_b + Psi_a(0) dPsi_b with Psi(0) = hi + lo
             const C psib = k.psi0[pb] + dpy[b];
             const C t = fma(dpx[a], psib,
-                            fma(dpx[a], k.psi0_lo[pb], fma(k.psi0[pa], dpy[b], k.psi0_lo[pa] * dpy[b])));
+                            fma(dpx[a], k.psi0_lo[pb],
+                                fma(k.psi0[pa], dpy[b],
+                                    UNBIASED ? fma(k.psi0_lo[pa], dpy[b], cr[ci])
+                                             : k.psi0_lo[pa] * dpy[b])));
             if constexpr (PACKED) {
                 geq[i] = fma(drho, k.w[ci], fma(rho, t, c3[ci]));
             } else {
-                const C vel = fma(rho, t, k.corr[ci]);
+                const C vel = UNBIASED ? rho_times(t) : fma(rho, t, k.corr[ci]);
                 geq[i] = fma(drho, k.w[ci], fma(drho, k.w_lo[ci], vel));
             }
         }
@@ -446,7 +472,7 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
         for (int i = 0; i < 9; ++i) {
             const C cu = C(cx_of(i)) * ux + C(cy_of(i)) * uy;
             const C poly = fma(C(3), cu, fma(C(4.5) * cu, cu, C(-1.5) * u2));
-            const C rp = rho * poly;
+            const C rp = rho_times(poly);
             const int ci = dcls(i);
             const C vel = fma(rp, k.w[ci], fma(rp, k.w_lo[ci], k.corr[ci]));
             geq[i] = fma(drho, k.w[ci], fma(drho, k.w_lo[ci], vel));
@@ -457,14 +483,14 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
 #pragma unroll
         for (int i = 0; i < 9; ++i) post[i] = fma(k.lam, g[i] - geq[i], geq[i]);
     } else {
-        const C sxx = C(0.5) * (dxy - rho * (ux2 - uy2));
-        const C sxy = pxy - rho * ux * uy;
+        const C sxx = C(0.5) * (dxy - rho_times(ux2 - uy2));
+        const C sxy = pxy - rho_times(ux * uy);
         C a;
         if constexpr (LOCAL) {
             const C th = k.theta + dth;
             a = k.lam / (C(2) * th * th * rho);
         } else {
-            a = k.lam * k.inv_2th2 * inv_rho;
+            a = k.lam * k.inv_2th2 * (UNBIASED ? inv_rho + inv_lo : inv_rho);
         }
         const C X[3] = {-ux, C(1) - ux, C(-1) - ux};
         const C Y[3] = {-uy, C(1) - uy, C(-1) - uy};

@@ -274,3 +274,27 @@ def test_autotune_picks_the_fastest_candidate_and_honours_the_cache(tmp_path):
     assert r2 == r and len(calls) == n                      # answered from the cache
     r3 = BT.autotune(BT_cases := W.batch_mix(16, seed=1), "f16", cache_path=path, measure=measure)
     assert len(calls) > n and BT.size_class(BT_cases) != BT.size_class(cases)
+
+
+def test_precision_router_rule():
+    """The half-noise ratio 1 / (u0 sqrt(N) gamma T) (gamma = theta (tau -
+    1/2) |k|^2, T the steps after the fit's start-up window): shock tubes and
+    FP32/FP64 batches are never rerouted; a shear wave moves to FP32 exactly
+    when the ratio exceeds the limit, and the ratio falls with amplitude,
+    size, viscosity and step count as that formula says."""
+    from paper_2501_16000_gb300.batch import FP16_NOISE_LIMIT, half_noise_ratio, route_storage
+    shock = W.shock_2048x4()
+    assert half_noise_ratio(shock) == 0.0 and route_storage(shock, "f16") == "f16"
+    c = W.LatticeCase(nx=64, ny=64, tau=0.6, case="shear", u0=0.05, m=1, n=0, steps=1000)
+    k2 = (2 * math.pi / 64) ** 2
+    want = 1.0 / (0.05 * 64 * (1 / 3) * 0.1 * k2 * (1000 - max(20, 20 * 0.6)))
+    assert abs(half_noise_ratio(c) / want - 1) < 1e-12
+    import dataclasses
+    assert half_noise_ratio(dataclasses.replace(c, u0=0.1)) == pytest.approx(want / 2)
+    assert half_noise_ratio(dataclasses.replace(c, ny=256)) == pytest.approx(want / 2)  # k along x
+    for st in ("f32", "f64"):
+        assert route_storage(dataclasses.replace(c, u0=1e-6), st) == st
+    for u0 in (1e-4, 1e-3, 1e-2, 0.1):
+        r = half_noise_ratio(dataclasses.replace(c, u0=u0))
+        assert route_storage(dataclasses.replace(c, u0=u0), "f16") == (
+            "f32" if r > FP16_NOISE_LIMIT else "f16")
