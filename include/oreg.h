@@ -252,6 +252,18 @@ olb_status olb_set_populations(olb_lattice *lat, const double *f9, int64_t t);
 olb_status olb_diagnostics(olb_lattice *lat, double *mass, double *mom_x, double *mom_y,
                            int64_t *nonfinite);
 
+/* Largest difference between the canonical populations of two lattices of
+ * the same size, in any storage formats: *max_abs_diff = max over nodes and
+ * directions of |f_a - f_b| and, if max_abs_ref is not NULL, *max_abs_ref =
+ * max |f_b| (b is the reference, e.g. an FP64 run of the same problem),
+ * both in FP64, reduced on the GPU over the whole lattice; a difference
+ * that is not finite reads as infinity.  Waits for b's stream, runs on a's
+ * and synchronises it.  Allocates 16 bytes of scratch with a on first use.
+ * OLB_ERR_INVALID for different sizes, OLB_ERR_STATE if one is not
+ * initialised. */
+olb_status olb_compare(olb_lattice *a, olb_lattice *b, double *max_abs_diff,
+                       double *max_abs_ref);
+
 /* FP64 projection of the velocity of S_t on a shear-wave mode:
  * A = (2 / (nx ny)) sum_x u(x) . e_perp sin(k . x), k = 2 pi (m/nx, n/ny);
  * the decay statistic of Sec. IV.  Synchronises the stream. */

@@ -72,6 +72,7 @@ SIGNATURES = {
     "olb_create_lattice": (ctypes.c_int, [_P(olb_params), _P(_h)]),
     "olb_set_option": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int64]),
     "olb_set_stream": (ctypes.c_int, [_h, ctypes.c_void_p]),
+    "olb_compare": (ctypes.c_int, [_h, _h, _d, _d]),
     "olb_init_shear_wave": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int32, ctypes.c_int32]),
     "olb_init_shear_flow": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_double,

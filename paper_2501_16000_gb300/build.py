@@ -32,6 +32,7 @@ UNITS = {
     "oreg_st_f32c64.cu": [],
     "oreg_batch.cu": [],
     "oreg_noalloc.cu": [],
+    "oreg_compare.cu": [],
 }
 
 

@@ -110,23 +110,6 @@ size_t pop_bytes(const olb_params *p) {
     return (size_t)nbuf * 9 * plane * elem_size(p->storage);
 }
 
-StateGeom geom(const olb_lattice *L) {
-    StateGeom g;
-    g.nx = L->p.nx;
-    g.ny = L->p.ny;
-    g.pitch = L->pitch;
-    g.plane = L->plane;
-    g.mode = L->p.layout == OLB_LAYOUT_AB ? STATE_AB : ((L->t & 1) ? STATE_AA_ODD : STATE_AA_EVEN);
-    return g;
-}
-
-// Buffer holding S_t.
-void *state_base(const olb_lattice *L) {
-    const size_t bytes = L->buf_elems * L->esize;
-    if (L->p.layout == OLB_LAYOUT_AA) return L->mem;
-    return static_cast<char *>(L->mem) + (size_t)(L->t & 1) * bytes;
-}
-
 #define DISPATCH(storage, fn, ...)                                      \
     ((storage) == OLB_F64   ? fn##_f64(__VA_ARGS__)                     \
      : (storage) == OLB_F32 ? fn##_f32(__VA_ARGS__)                     \
@@ -752,6 +735,7 @@ olb_status olb_destroy(olb_lattice *L) {
     }
     if (L->d_chunk) cudaFree(L->d_chunk);
     if (L->d_tab) cudaFree(L->d_tab);
+    if (L->d_cmp) cudaFree(L->d_cmp);
     if (L->h_tab) cudaFreeHost(L->h_tab);
     if (L->stream != L->owned_stream && L->owned_stream) {
         cudaError_t e = cudaStreamSynchronize(L->owned_stream);

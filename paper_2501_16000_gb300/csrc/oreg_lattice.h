@@ -9,6 +9,7 @@
 
 #include "oreg.h"
 #include "oreg_device.cuh"
+#include "oreg_launch.h"
 
 struct olb_batch;
 
@@ -47,6 +48,7 @@ struct olb_lattice {
     oreg::CollConst<double> kd;     // FP64 constants (shift as stored type's shift)
     oreg::CollConst<float> kf;      // FP32 constants (F32, F16, BF16 compute)
     olb_batch *batch;               // batch the lattice currently belongs to, or NULL
+    unsigned long long *d_cmp;      // olb_compare result scratch (lazy)
 };
 
 namespace oreg {
@@ -66,5 +68,23 @@ struct NvtxRange {
 inline int kernel_eq(const olb_params *p) {
     if (p->eq == OLB_EQ_GUIDED && p->theta_mode == OLB_THETA_LOCAL) return EQ_GUIDED_LOCAL;
     return p->eq == OLB_EQ_GUIDED ? EQ_GUIDED : EQ_POLY2;
+}
+
+// Geometry of the lattice's canonical state at its current time.
+inline StateGeom geom(const olb_lattice *L) {
+    StateGeom g;
+    g.nx = L->p.nx;
+    g.ny = L->p.ny;
+    g.pitch = L->pitch;
+    g.plane = L->plane;
+    g.mode = L->p.layout == OLB_LAYOUT_AB ? STATE_AB : ((L->t & 1) ? STATE_AA_ODD : STATE_AA_EVEN);
+    return g;
+}
+
+// Buffer holding S_t.
+inline void *state_base(const olb_lattice *L) {
+    const size_t bytes = L->buf_elems * L->esize;
+    if (L->p.layout == OLB_LAYOUT_AA) return L->mem;
+    return static_cast<char *>(L->mem) + (size_t)(L->t & 1) * bytes;
 }
 }  // namespace oreg

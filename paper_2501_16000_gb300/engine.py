@@ -240,6 +240,13 @@ class Lattice:
             B.check(st, "olb_diagnostics")
         return {"mass": m.value, "mom_x": jx.value, "mom_y": jy.value, "nonfinite": nf.value}
 
+    def compare(self, ref: "Lattice") -> tuple[float, float]:
+        """(max |f - f_ref|, max |f_ref|) over all populations of the two
+        lattices' canonical states (olb_compare, reduced on the GPU)."""
+        d, r = ctypes.c_double(), ctypes.c_double()
+        B.call("olb_compare", self.handle, ref.handle, ctypes.byref(d), ctypes.byref(r))
+        return d.value, r.value
+
     def wave_amplitude(self, m: int, n: int) -> float:
         a = ctypes.c_double()
         B.call("olb_wave_amplitude", self.handle, int(m), int(n), ctypes.byref(a))
