@@ -6,7 +6,7 @@ seed 0, theta = 1/3, tau = 0.6, u0 = 0.05), guided equilibrium, OReg
 collision, FP32 storage and compute, A-B layout.  One "step" is one lattice
 time step (gather, moments, equilibrium, OReg projection, relaxation, store);
 the FP64 diagnostics reduction (mass, momentum, non-finite count) runs every
-100 steps inside the timed region.
+100 steps and after the last step, inside the timed region.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead (bounded sample of the same workload).
@@ -335,7 +335,7 @@ def run_native(args):
             lat.step(1)
             ev[s][1].record(stream)
             launches += 1
-            if (s + 1) % DIAG_EVERY == 0:
+            if (s + 1) % DIAG_EVERY == 0 or s + 1 == K:
                 d = lat.diagnostics()          # FP64 mass/momentum/non-finite check
                 launches += 2
                 if d["nonfinite"]:
@@ -410,7 +410,9 @@ def run_native(args):
             "config": {"workload": f"shear{case.nx}x{case.ny}-oreg-guided-{args.layout}",
                        "nodes": N, "theta": case.theta, "tau": case.tau, "u0": case.u0,
                        "wave": [case.m, case.n], "storage": args.storage,
-                       "layout": args.layout, "diagnostics_every": DIAG_EVERY,
+                       "layout": args.layout,
+                       "diagnostics": f"FP64 mass/momentum/non-finite check every {DIAG_EVERY} "
+                                      f"steps and after the last, inside the timed region",
                        "exact_conserved_sums": (args.comp if args.comp is not None else
                                                 int(args.storage == "f32")),
                        "warps_per_block": args.warps,
