@@ -158,11 +158,10 @@ __device__ __forceinline__ CollConst<F2> broadcast(const CollConst<float> &k) {
 // (HBM-bound) stays scalar, where packing measured no faster for A-B and
 // slower for AA.
 //
-// FP32 with exact conserved sums: PAIR_SUMS forms them for node pairs with
-// packed arithmetic (the A-B kernels: as fast as plain sums there); the
-// in-place AA kernels, at their register cap, form them per node (packing
-// spills there).  Both round every operation alike: the results are the same.
-template <int S, int EQ, int COLL, bool EXACT, bool PAIR_SUMS = true>
+// FP32 with exact conserved sums forms them for node pairs with packed
+// arithmetic (measured faster than per node in every layout; each lane
+// rounds as the scalar operation, so the results are the same).
+template <int S, int EQ, int COLL, bool EXACT>
 __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<S>::V],
                                             const CollConst<typename Storage<S>::C> &k) {
     using C = typename Storage<S>::C;
@@ -180,7 +179,7 @@ __device__ __forceinline__ void collide_vec(typename Storage<S>::C f[9][Storage<
                 f[i][j + 1] = post[i].hi();
             }
         }
-    } else if constexpr (S == ST_F32 && EXACT && PAIR_SUMS) {
+    } else if constexpr (S == ST_F32 && EXACT) {
         // the exact conserved sums of node pairs with packed arithmetic (the
         // split costs ~50 additions per node), the rest of the collision scalar
         CollConst<F2> k2;
@@ -372,7 +371,7 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
 #pragma unroll
         for (int j = 0; j < V; ++j) f[i][j] = ST::dec_step(v.e[j]);
     }
-    collide_vec<S, EQ, COLL, EXACT, false>(f, k);
+    collide_vec<S, EQ, COLL, EXACT>(f, k);
     if constexpr (WALLS) {
         if (lane_has_wall<S>(xb, nx))
             bounce_back_walls<S, STATE_AA_EVEN>(A, plane, pitch, y, ny, xb, nx, f);
@@ -429,7 +428,7 @@ __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, i
     C f[9][V];
     pull_all<S, true>(A, plane, pitch, y, ny, xb, nx, sub, W, f);
 
-    collide_vec<S, EQ, COLL, EXACT, false>(f, k);
+    collide_vec<S, EQ, COLL, EXACT>(f, k);
     if constexpr (WALLS) {
         if (lane_has_wall<S>(xb, nx))
             bounce_back_walls<S, STATE_AA_ODD>(A, plane, pitch, y, ny, xb, nx, f);
