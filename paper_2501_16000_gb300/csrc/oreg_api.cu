@@ -34,6 +34,9 @@ olb_status fail(olb_status st, const char *fmt, ...) {
 }
 
 olb_status cuda_fail(cudaError_t e, const char *what) {
+    // a failed allocation is not sticky, but it stays the thread's last error:
+    // clear it, so that the next launch check of this thread does not report it
+    if (e == cudaErrorMemoryAllocation) (void)cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? OLB_ERR_NOMEM : OLB_ERR_CUDA, "%s: %s (%s)",
                 what, cudaGetErrorString(e), cudaGetErrorName(e));
 }

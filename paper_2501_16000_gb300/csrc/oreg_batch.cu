@@ -31,6 +31,7 @@ olb_status bfail(olb_status st, const char *fmt, ...) {
 }
 
 olb_status bcuda(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) (void)cudaGetLastError();  // not sticky: clear it
     return bfail(e == cudaErrorMemoryAllocation ? OLB_ERR_NOMEM : OLB_ERR_CUDA, "%s: %s", what,
                  cudaGetErrorString(e));
 }

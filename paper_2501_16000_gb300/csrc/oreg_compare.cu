@@ -87,6 +87,7 @@ cudaError_t launch_b(const olb_lattice *A, const olb_lattice *B, unsigned long l
 
 olb_status cmp_fail(olb_status st, const char *what, cudaError_t e = cudaSuccess) {
     char msg[256];
+    if (e == cudaErrorMemoryAllocation) (void)cudaGetLastError();  // not sticky: clear it
     if (e != cudaSuccess) snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
     else snprintf(msg, sizeof msg, "%s", what);
     set_last_error_message(msg);

@@ -296,6 +296,28 @@ def test_set_get_roundtrip(storage, layout):
                 assert np.abs(got - f0).max() <= eps * 0.5 + 1e-12
 
 
+def test_failed_allocation_is_reported_and_harmless():
+    """A lattice larger than the GPU's memory (the library allocating its
+    populations) and a batch with an impossible item table fail with
+    OLB_ERR_NOMEM and a message; afterwards a normal lattice still steps and
+    matches the oracle (the failed allocation leaves no error behind)."""
+    import ctypes
+
+    from paper_2501_16000_gb300 import binding as B
+    from paper_2501_16000_gb300.engine import make_params
+    lib = B.load()
+    p = make_params(nx=200000, ny=200000, tau=0.8, storage="f64")      # ~5.8 TB of populations
+    h = ctypes.c_void_p()
+    assert lib.olb_create_lattice(ctypes.byref(p), ctypes.byref(h)) == B.OLB_ERR_NOMEM
+    assert "allocating" in lib.olb_last_error().decode()
+    bp = B.olb_batch_params(B.OLB_F16_SHIFTED, B.OLB_LAYOUT_AB, 4, 1 << 40, 4, 4, 0, None, 0)
+    hb = ctypes.c_void_p()
+    assert lib.olb_batch_create(ctypes.byref(bp), ctypes.byref(hb)) == B.OLB_ERR_NOMEM
+    case = SHEAR_64[0]
+    err = rel_linf(gpu_run(case, 20, "f32", "ab"), oracle_run(case, 20))
+    assert err <= TOL["f32"], err
+
+
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 def test_checkpoint_resume_is_bitwise(layout):
     from paper_2501_16000_gb300.engine import Lattice
