@@ -118,12 +118,13 @@ typedef enum {
        momentum) of the FP32 collision are exact sums of the stored
        populations, rounded once (an error-free split of each population
        against a power-of-two constant; about 50 more FP32 additions per
-       node).  Plain FP32 sums round each partial sum, and the rounding
-       repeats identically at every node of a uniform region and every
-       step: on the 2048 x 4 shock tube (tau = 0.51, 2000 steps) they end
-       ~3e-5 from the FP64 scheme, the exact sums ~5e-6.  0: plain sums
-       (olb_batch_add rejects an FP32 lattice with 0).  Ignored by the other
-       formats. */
+       node, two nodes per packed instruction).  Plain FP32 sums round each
+       partial sum, and the rounding repeats identically at every node of a
+       uniform region and every step: on the 2048 x 4 shock tube (tau =
+       0.51, 2000 steps) they end ~3e-5 from the FP64 scheme, the exact
+       sums ~5e-6.  0: plain sums (the rest of the FP32 collision is the
+       same; olb_batch_add rejects an FP32 lattice with 0).  Ignored by the
+       other formats. */
     OLB_OPT_COMPENSATED = 1,
     /* warps per thread block of the stream-collide kernels: 1, 2, 4 or 8
        (default 4).  A warp updates 32/W row segments of W*V consecutive
