@@ -283,9 +283,10 @@ olb_status olb_wave_mode(olb_lattice *lat, int32_t m, int32_t n, double *a_sin,
 /* ------------------------------------------------------------------------
  * Batched path: many independent lattices advanced together.
  *
- * One persistent kernel per time step walks a flattened table of warp work
- * items (one row segment of one member lattice each); steps_per_launch such
- * launches are captured once in a CUDA graph and replayed per round.  Each
+ * One persistent kernel per time step and slot walks a flattened table of
+ * warp work items (row groups of one row segment of one member lattice
+ * each); steps_per_launch steps of such launches are captured in a CUDA
+ * graph and replayed per round.  Each
  * member keeps its own size, relaxation time, temperature, equilibrium and
  * collision; all members share the batch's storage format and layout and
  * must have been created on the batch's stream.  Members are grouped into

@@ -2,14 +2,15 @@
 // lattices of any size by one time step, walking a flattened table of warp
 // work items (one row segment of one lattice each).
 //
-// Every lattice keeps its own population memory, geometry, relaxation time
-// and equilibrium constants in a device descriptor.  A device-resident global
-// step counter g decides, per lattice, whether it is active in this launch
-// (g_base <= g < g_end) and at which local time t = t_base + (g - g_base),
-// which selects the A-B buffer or the AA parity.  The launches of K steps and
-// one counter increment are captured once in a CUDA graph; joining and
-// leaving lattices only rewrite the descriptor, item and group tables, so the
-// graph is never re-captured.
+// Every lattice keeps its own population memory, geometry and relaxation
+// time in a device descriptor; the rest of its collision constants belong to
+// its slot (below).  A device-resident global step counter g decides, per
+// lattice, whether it is active in this launch (g_base <= g < g_end) and at
+// which local time t = t_base + (g - g_base), which selects the A-B buffer or
+// the AA parity.  The launches of K steps and one counter increment are
+// captured in a CUDA graph; joining and leaving lattices only rewrite the
+// descriptor, item and group tables (stream-ordered copies), and the graph is
+// captured again only when a lattice brings a new slot.
 #pragma once
 
 #include <cuda_runtime.h>
