@@ -283,8 +283,8 @@ olb_status olb_wave_mode(olb_lattice *lat, int32_t m, int32_t n, double *a_sin,
 /* ------------------------------------------------------------------------
  * Batched path: many independent lattices advanced together.
  *
- * One persistent kernel per time step and slot walks a flattened table of
- * warp work items (row groups of one row segment of one member lattice
+ * One kernel per time step and slot, whose warps stride over a flattened
+ * table of warp work items (row groups of one row segment of one member lattice
  * each); steps_per_launch steps of such launches are captured in a CUDA
  * graph and replayed per round.  Each
  * member keeps its own size, relaxation time, temperature, equilibrium and
@@ -316,8 +316,11 @@ typedef struct {
                                   of 32 / W rows of one segment) */
     int32_t steps_per_launch;  /* K: time steps per graph replay (1..10000) */
     int32_t warps_per_block;   /* 1, 2 or 4 */
-    int32_t blocks_per_sm;     /* persistent grid = blocks_per_sm x SMs;
-                                  0 = the kernel's occupancy limit */
+    int32_t blocks_per_sm;     /* grid = blocks_per_sm x SMs (0..256);
+                                  0 = the kernel's occupancy limit (every
+                                  block resident); above it, blocks start as
+                                  earlier ones finish, which evens out uneven
+                                  work items */
     void *cuda_stream;         /* stream of the batch and of every member;
                                   NULL: the library creates and owns one */
     int32_t item_row_groups;   /* R: row groups per work item (1..64); a warp

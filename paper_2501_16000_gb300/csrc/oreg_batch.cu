@@ -317,8 +317,8 @@ olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out) {
     if (p->warps_per_block < 1 || 32 * p->warps_per_block > BATCH_MAX_THREADS ||
         (p->warps_per_block & (p->warps_per_block - 1)))
         return bfail(OLB_ERR_INVALID, "warps_per_block must be 1, 2 or 4");
-    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32)
-        return bfail(OLB_ERR_INVALID, "blocks_per_sm must be in [0, 32] (0 = occupancy limit)");
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 256)
+        return bfail(OLB_ERR_INVALID, "blocks_per_sm must be in [0, 256] (0 = occupancy limit)");
     if (p->item_row_groups < 0 || p->item_row_groups > 64)
         return bfail(OLB_ERR_INVALID, "item_row_groups must be in [0, 64] (0 = %d)",
                      BATCH_ITEM_ROW_GROUPS);

@@ -1,6 +1,8 @@
-// Batched stream-collide: one persistent kernel advances many independent
-// lattices of any size by one time step, walking a flattened table of warp
-// work items (one row segment of one lattice each).
+// Batched stream-collide: one kernel advances many independent lattices of
+// any size by one time step, its warps striding over a flattened table of
+// warp work items (row groups of one row segment of one lattice each).  The
+// grid is either resident as a whole (persistent) or oversubscribed, so that
+// blocks start as earlier ones finish.
 //
 // Every lattice keeps its own population memory, geometry and relaxation
 // time in a device descriptor; the rest of its collision constants belong to

@@ -29,16 +29,17 @@ def mixed_cases():
     return cases + extra
 
 
+@pytest.mark.parametrize("blocks", [0, 256])           # every block resident / oversubscribed
 @pytest.mark.parametrize("storage", ["f16", "f32", "bf16"])
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-def test_batch_equals_alone_bitwise(storage, layout):
+def test_batch_equals_alone_bitwise(storage, layout, blocks):
     from paper_2501_16000_gb300.batch import BatchEngine
     from paper_2501_16000_gb300.engine import Lattice
     cases = mixed_cases()
     K = 7
     steps = [5 + 3 * j for j in range(len(cases))]        # odd and even totals, mid-round ends
     with BatchEngine(storage, layout, max_lattices=64, max_items=1 << 16, steps_per_launch=K,
-                     warps_per_block=4) as eng:
+                     warps_per_block=4, blocks_per_sm=blocks) as eng:
         lats = []
         for j, c in enumerate(cases):
             lat = eng.new_lattice(c)
@@ -148,6 +149,14 @@ def test_nonfinite_member_stays_isolated():
         assert lats[1].diagnostics(raise_nonfinite=False)["nonfinite"] > 100
         for lat in lats:
             lat.close()
+
+
+def test_batch_rejects_a_grid_beyond_256_blocks_per_sm():
+    from paper_2501_16000_gb300 import binding as B
+    from paper_2501_16000_gb300.batch import BatchEngine
+    with pytest.raises(B.OregError) as e:
+        BatchEngine("f16", "ab", max_lattices=4, max_items=1 << 12, blocks_per_sm=257)
+    assert e.value.status == B.OLB_ERR_INVALID
 
 
 def test_batch_rejects_a_lattice_with_the_fp64_collision():

@@ -251,7 +251,7 @@ def test_autotune_picks_the_fastest_candidate_and_honours_the_cache(tmp_path):
         c = 1.0
         c += {"ab": 0.0, "aa": 0.3}[cfg["layout"]]
         c += {1: 0.2, 2: 0.05, 4: 0.0}[cfg["warps_per_block"]]
-        c += {0: 0.0, 1: 0.4, 2: 0.1}[cfg["blocks_per_sm"]]
+        c += {0: 0.0, 2: 0.1, 32: 0.03, 64: 0.2, 128: 0.4}[cfg["blocks_per_sm"]]
         c += {1: 0.08, 2: 0.0, 4: 0.02, 8: 0.05}[cfg["item_row_groups"]]
         c += {25: 0.04, 50: 0.02, 100: 0.0, 200: 0.01}[cfg["steps_per_launch"]]
         return c
