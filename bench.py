@@ -58,7 +58,7 @@ def parse_args():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched section and print its JSON (profiling)")
     ap.add_argument("--batch-config", default=None,
-                    help="layout,warps_per_block,blocks_per_sm,item_row_groups,steps_per_launch "
+                    help="layout,warps_per_block,blocks_per_sm,item_passes,steps_per_launch "
                          "instead of the autotuner (e.g. ab,2,0,2,100)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=1000)
@@ -445,7 +445,7 @@ def _timed_batch_solve(groups, tuned, steps):
     states created and initialised outside the timed region."""
     import torch
     from paper_2501_16000_gb300.batch import BatchEngine, work_items
-    K, R = tuned["steps_per_launch"], tuned["item_row_groups"]
+    K, R = tuned["steps_per_launch"], tuned["item_passes"]
     engines = []
     for storage, cases in groups.items():
         if cases:
@@ -454,7 +454,7 @@ def _timed_batch_solve(groups, tuned, steps):
                                         max_items=items, steps_per_launch=K,
                                         warps_per_block=tuned["warps_per_block"],
                                         blocks_per_sm=tuned["blocks_per_sm"],
-                                        item_row_groups=R), cases))
+                                        item_passes=R), cases))
     try:
         for rep in range(2):
             lats = []
@@ -482,7 +482,7 @@ def _timed_batch_solve(groups, tuned, steps):
 def batched_section(args):
     """Batched workload: 512 independent uneven lattices (shear waves and shock
     tubes), FP16 storage (stochastic rounding) / FP32 compute, autotuned batch
-    (layout, block shape, grid, row groups per work item, steps per CUDA-graph
+    (layout, block shape, grid, warp passes per work item, steps per CUDA-graph
     replay).  Timed twice: every lattice in FP16, and with precision routing
     (shear waves whose decay rate FP16 cannot resolve to 1e-4 run in an FP32
     batch beside the FP16 one); against serial plain FP32 single-lattice
@@ -501,7 +501,7 @@ def batched_section(args):
     if args.batch_config:
         lay, w, b, r, k = args.batch_config.split(",")
         tuned = {"layout": lay, "warps_per_block": int(w), "blocks_per_sm": int(b),
-                 "item_row_groups": int(r), "steps_per_launch": int(k), "given": True}
+                 "item_passes": int(r), "steps_per_launch": int(k), "given": True}
     else:
         tuned = autotune(cases, "f16", use_cache=False)
     t_tune = time.perf_counter() - t_tune
@@ -591,7 +591,7 @@ def serving_section(args, batched):
                      steps_per_launch=tuned["steps_per_launch"],
                      warps_per_block=tuned["warps_per_block"],
                      blocks_per_sm=tuned["blocks_per_sm"],
-                     item_row_groups=tuned["item_row_groups"])
+                     item_passes=tuned["item_passes"])
         res, wall = srv.run(unit, time_scale=time_scale)
         stats = summarize(res, wall, label)
         stats.update({"budget_gb": round(budget / 1e9, 3), "rounds": srv.rounds,

@@ -127,9 +127,10 @@ typedef enum {
        other formats. */
     OLB_OPT_COMPENSATED = 1,
     /* warps per thread block of the stream-collide kernels: 1, 2, 4 or 8
-       (default 4).  A warp updates 32/W row segments of W*V consecutive
-       nodes, V = 16 bytes / element size and W the smallest power of two
-       <= 32 with W * V >= nx. */
+       (default 4).  A warp pass updates 32 consecutive 16-byte vectors of
+       V nodes each (V = 16 bytes / element size) of the row-major planes,
+       whose rows are nx rounded up to V elements, back to back; a pass may
+       span rows. */
     OLB_OPT_WARPS_PER_BLOCK = 2,
     /* 1 (default for OLB_F16_SHIFTED and OLB_BF16_SHIFTED): round the
        post-collision values to the half format stochastically, with random
@@ -152,8 +153,8 @@ typedef enum {
     OLB_OPT_F64_COLLISION = 4
 } olb_option;
 
-/* Version of this ABI (bumped on incompatible change); 4 since
- * olb_batch_params.item_row_groups. */
+/* Version of this ABI (bumped on incompatible change); 5 since
+ * olb_batch_params.item_passes (work items of warp passes). */
 int32_t olb_abi_version(void);
 
 /* Bytes of device memory the populations of a lattice with these
@@ -169,7 +170,11 @@ size_t olb_required_bytes(const olb_params *p);
 
 /* Validates p, allocates the lattice and (unless p->device_buffer is
  * given) its population memory.  The state is undefined until one of the
- * olb_init_* or olb_set_populations calls.  *out receives the handle. */
+ * olb_init_* or olb_set_populations calls.  *out receives the handle.
+ * OLB_ERR_INVALID for a lattice of more than 2^36 nodes or more than
+ * 2^31 - 64 16-byte vectors per population plane (ceil(nx / V) x ny,
+ * V = 16 / element size); OLB_ERR_NOMEM when its memory cannot be
+ * allocated. */
 olb_status olb_create_lattice(const olb_params *p, olb_lattice **out);
 
 /* Rebinds a lattice to another stream: the work of every later call on it
@@ -284,9 +289,9 @@ olb_status olb_wave_mode(olb_lattice *lat, int32_t m, int32_t n, double *a_sin,
  * Batched path: many independent lattices advanced together.
  *
  * One kernel per time step and slot, whose warps stride over a flattened
- * table of warp work items (row groups of one row segment of one member lattice
- * each); steps_per_launch steps of such launches are captured in a CUDA
- * graph and replayed per round.  Each
+ * table of warp work items (up to item_passes consecutive warp passes over
+ * one member lattice each); steps_per_launch steps of such launches are
+ * captured in a CUDA graph and replayed per round.  Each
  * member keeps its own size, relaxation time, temperature, equilibrium and
  * collision; all members share the batch's storage format and layout and
  * must have been created on the batch's stream.  Members are grouped into
@@ -308,12 +313,10 @@ typedef struct {
     int32_t layout;            /* olb_layout of every member */
     int32_t max_lattices;      /* descriptor capacity */
     int64_t max_items;         /* work-item capacity: sum over members of
-                                  ceil(ceil(ny / (32 / W)) / R) * ceil(nx / (W * V)),
-                                  V = 16 / element size, W the lanes per row
-                                  segment (a power of two <= 32, the one with
-                                  the fewest warp passes over the lattice), R
-                                  = item_row_groups (an item is up to R groups
-                                  of 32 / W rows of one segment) */
+                                  ceil(P / R), P = ceil(ceil(nx / V) * ny / 32)
+                                  the member's warp passes (32 vectors of
+                                  V = 16 / element size nodes each, rows
+                                  rounded up to V), R = item_passes */
     int32_t steps_per_launch;  /* K: time steps per graph replay (1..10000) */
     int32_t warps_per_block;   /* 1, 2 or 4 */
     int32_t blocks_per_sm;     /* grid = blocks_per_sm x SMs (0..256);
@@ -323,9 +326,9 @@ typedef struct {
                                   work items */
     void *cuda_stream;         /* stream of the batch and of every member;
                                   NULL: the library creates and owns one */
-    int32_t item_row_groups;   /* R: row groups per work item (1..64); a warp
-                                  reads the member's descriptor once per item;
-                                  0 = 4 */
+    int32_t item_passes;       /* R: warp passes per work item (1..64); a
+                                  warp reads the member's descriptor once
+                                  per item; 0 = 4 */
 } olb_batch_params;
 
 olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out);

@@ -1,9 +1,9 @@
-"""Batched path: many independent lattices in one persistent launch per step,
+"""Batched path: many independent lattices in one launch per step (and slot),
 steps_per_launch steps per CUDA-graph replay (C ABI ``olb_batch_*``).
 
 ``BatchEngine`` owns the batch and a torch stream; its lattices are created on
 that stream with torch-allocated population memory.  ``autotune`` picks the
-layout, warps per block, persistent-grid size, row groups per work item and
+layout, warps per block, grid size, warp passes per work item and
 steps per graph replay for a workload by timing graph replays, and caches the
 choice per (ABI, storage, size class).
 """
@@ -22,43 +22,36 @@ from .engine import LAYOUT, STORAGE, Lattice
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
-ITEM_ROW_GROUPS = 4   # the library's default row groups per work item
+ITEM_PASSES = 4   # the library's default warp passes per work item
 
 
-def segment_lanes(nx: int, ny: int, v: int) -> int:
-    """Lanes W per row segment, as the library chooses them: a warp pass covers
-    32/W rows of one W-lane segment of W*v nodes, and W (a power of two <= 32)
-    needs the fewest passes; among equal counts the widest."""
-    best, best_passes = 32, None
-    for w in (32, 16, 8, 4, 2, 1):
-        passes = math.ceil(nx / (w * v)) * math.ceil(ny / (32 // w))
-        if best_passes is None or passes < best_passes:
-            best, best_passes = w, passes
-    return best
+def warp_passes(nx: int, ny: int, v: int) -> int:
+    """Warp passes over a lattice, as the library makes them: 32 consecutive
+    vectors of v nodes each of the row-major planes, whose rows hold nx
+    rounded up to v nodes, back to back."""
+    return math.ceil(math.ceil(nx / v) * ny / 32)
 
 
-def work_items(nx: int, ny: int, storage: str, row_groups: int = ITEM_ROW_GROUPS) -> int:
-    """Warp work items of one lattice: a warp pass covers a row group of 32/W
-    rows of one W-lane row segment (``segment_lanes``); an item is up to
-    `row_groups` row groups of one segment."""
+def work_items(nx: int, ny: int, storage: str, passes: int = ITEM_PASSES) -> int:
+    """Warp work items of one lattice: up to `passes` consecutive warp passes
+    (``warp_passes``) each."""
     v = 16 // {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[storage]
-    w = segment_lanes(nx, ny, v)
-    return math.ceil(math.ceil(ny / (32 // w)) / row_groups) * math.ceil(nx / (w * v))
+    return math.ceil(warp_passes(nx, ny, v) / passes)
 
 
 class BatchEngine:
     def __init__(self, storage="f16", layout="ab", max_lattices=1024, max_items=1 << 22,
                  steps_per_launch=100, warps_per_block=4, blocks_per_sm=0, stream=None,
-                 item_row_groups=ITEM_ROW_GROUPS):
+                 item_passes=ITEM_PASSES):
         import torch
         self.storage, self.layout = storage, layout
         self.steps_per_launch = int(steps_per_launch)
-        self.item_row_groups = int(item_row_groups)
+        self.item_passes = int(item_passes)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.params = B.olb_batch_params(STORAGE[storage], LAYOUT[layout], int(max_lattices),
                                          int(max_items), int(steps_per_launch),
                                          int(warps_per_block), int(blocks_per_sm),
-                                         self.stream.cuda_stream, int(item_row_groups))
+                                         self.stream.cuda_stream, int(item_passes))
         h = ctypes.c_void_p()
         B.check(B.load().olb_batch_create(ctypes.byref(self.params), ctypes.byref(h)),
                 "olb_batch_create")
@@ -179,19 +172,19 @@ def size_class(cases) -> str:
 
 # Search space of the tuner.  The stages run in this order, each over one
 # group of parameters with the best values found so far for the others:
-# (layout, warps per block, blocks per SM), then row groups per work item,
+# (layout, warps per block, blocks per SM), then warp passes per work item,
 # then steps per graph replay.  Blocks per SM above the resident count (0)
 # oversubscribe the grid: its warps still stride over the work items, but
 # blocks start as earlier ones finish, so the block scheduler evens out a mix
 # of uneven items (on the 512-lattice FP16 mix: 121 GLUPS with every block
-# resident, 126 with 64 blocks per SM and 4 row groups per item).
+# resident, 126 with 64 blocks per SM and 4 warp passes per item).
 TUNE_STAGES = (
     {"layout": ("ab", "aa"), "warps_per_block": (1, 2, 4), "blocks_per_sm": (0, 2, 32, 64, 128)},
-    {"item_row_groups": (1, 2, 4, 8)},
+    {"item_passes": (1, 2, 4, 8)},
     {"steps_per_launch": (25, 50, 100, 200)},
 )
 TUNE_START = {"layout": "ab", "warps_per_block": 4, "blocks_per_sm": 0,
-              "item_row_groups": ITEM_ROW_GROUPS, "steps_per_launch": 50}
+              "item_passes": ITEM_PASSES, "steps_per_launch": 50}
 
 
 def _grid(stage: dict):
@@ -211,10 +204,10 @@ def measure_replays(cases, storage: str, cfg: dict, repeats: int, lattices=None)
     lattices = {} if lattices is None else lattices
     K = int(cfg["steps_per_launch"])
     stream = lattices.setdefault("_stream", torch.cuda.Stream())
-    items = sum(work_items(c.nx, c.ny, storage, cfg["item_row_groups"]) for c in cases)
+    items = sum(work_items(c.nx, c.ny, storage, cfg["item_passes"]) for c in cases)
     with BatchEngine(storage, cfg["layout"], max_lattices=len(cases), max_items=items,
                      steps_per_launch=K, warps_per_block=cfg["warps_per_block"],
-                     blocks_per_sm=cfg["blocks_per_sm"], item_row_groups=cfg["item_row_groups"],
+                     blocks_per_sm=cfg["blocks_per_sm"], item_passes=cfg["item_passes"],
                      stream=stream) as eng:
         if cfg["layout"] not in lattices:
             lattices[cfg["layout"]] = [eng.new_lattice(c) for c in cases]
@@ -237,7 +230,7 @@ def measure_replays(cases, storage: str, cfg: dict, repeats: int, lattices=None)
 def autotune(cases, storage="f16", stages=TUNE_STAGES, start=None, repeats=3, use_cache=True,
              cache_path=None, measure=None, verbose=False):
     """Chooses the batch configuration for a workload: layout, warps per block,
-    blocks per SM, row groups per work item and steps per graph replay.
+    blocks per SM, warp passes per work item and steps per graph replay.
 
     Each candidate is timed as the median ms per step of `repeats` graph
     replays (``measure_replays``, or `measure(cfg) -> [ms, ...]`); the stages

@@ -48,7 +48,7 @@ class olb_params(ctypes.Structure):
                 ("theta_mode", ctypes.c_int32)]
 
 
-ABI_VERSION = 4
+ABI_VERSION = 5
 BOUNDARY = {"periodic": 0, "walls_x": 1}
 THETA_MODE = {"fixed": 0, "local": 1}
 
@@ -58,7 +58,7 @@ class olb_batch_params(ctypes.Structure):
                 ("max_lattices", ctypes.c_int32), ("max_items", ctypes.c_int64),
                 ("steps_per_launch", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
-                ("item_row_groups", ctypes.c_int32)]
+                ("item_passes", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER

@@ -85,6 +85,13 @@ olb_status validate(const olb_params *p) {
     if (p->coll != OLB_COLL_OREG && p->coll != OLB_COLL_BGK)
         return fail(OLB_ERR_INVALID, "unknown collision %d", p->coll);
     if (elem_size(p->storage) == 0) return fail(OLB_ERR_INVALID, "unknown storage %d", p->storage);
+    {
+        // the kernels index the 16-byte vectors of a population plane with an int
+        const int V = vec_elems(p->storage);
+        if ((int64_t)((p->nx + V - 1) / V) * p->ny > (int64_t)INT32_MAX - 64)
+            return fail(OLB_ERR_INVALID, "lattice too large: %d x %d (over 2^31 vectors per plane)",
+                        p->nx, p->ny);
+    }
     if (p->layout != OLB_LAYOUT_AB && p->layout != OLB_LAYOUT_AA)
         return fail(OLB_ERR_INVALID, "unknown layout %d", p->layout);
     if (p->eq == OLB_EQ_GUIDED && !(p->theta > 0 && p->theta < 1))
@@ -260,7 +267,7 @@ olb_status mode_tables(olb_lattice *L, int m, int n) {
 
 extern "C" {
 
-int32_t olb_abi_version(void) { return 4; }
+int32_t olb_abi_version(void) { return 5; }
 
 size_t olb_required_bytes(const olb_params *p) {
     if (validate(p) != OLB_OK) return 0;
@@ -481,8 +488,7 @@ olb_status olb_step(olb_lattice *L, int64_t nsteps) {
     a.ny = L->p.ny;
     a.pitch = L->pitch;
     a.plane = L->plane;
-    a.lw = segment_log2(L->p.nx, L->p.ny, L->V);
-    a.segs = (L->p.nx + (L->V << a.lw) - 1) / (L->V << a.lw);
+    a.passes = (int)warp_passes(L->pitch, L->p.ny, L->V);
     a.eq = kernel_eq(&L->p);
     a.coll = L->p.coll;
     a.layout = L->p.layout;

@@ -99,7 +99,6 @@ void fill_desc(void *dst, const Member &m, C lam) {
     d.pitch = L->pitch;
     d.eq = L->p.eq;
     d.coll = L->p.coll;
-    d.lw = segment_log2(L->p.nx, L->p.ny, L->V);
     d.plane = L->plane;
     d.buf_elems = L->buf_elems;
     d.t_base = m.t_base;
@@ -203,16 +202,11 @@ olb_status upload(olb_batch *b) {
         else fill_desc<float>(&b->h_descs[j * b->desc_size], m, L->kf.lam);
         const int cls = (int)((m.t_base - m.g_base) & 1);
         const int grp = m.slot * 2 + cls;
-        const int lw = segment_log2(L->p.nx, L->p.ny, L->V);
-        const int segs = (L->p.nx + (L->V << lw) - 1) / (L->V << lw);
-        const int rows = 32 >> lw;  // rows per row group (one warp pass)
-        const int ngroups = (L->p.ny + rows - 1) / rows;
-        const int R = b->p.item_row_groups;
-        for (int q = 0; q < ngroups; q += R) {
-            const int count = std::min(R, ngroups - q);
-            for (int s = 0; s < segs; ++s)
-                per_group[grp].push_back(make_int4((int)j, q * rows, s, count));
-        }
+        // item: (member, first vector, 0, warp passes of 32 vectors)
+        const int passes = (int)warp_passes(L->pitch, L->p.ny, L->V);
+        const int R = b->p.item_passes;
+        for (int q = 0; q < passes; q += R)
+            per_group[grp].push_back(make_int4((int)j, q * 32, 0, std::min(R, passes - q)));
     }
     b->h_items.clear();
     for (int q = 0; q < NGROUPS; ++q) {
@@ -319,13 +313,13 @@ olb_status olb_batch_create(const olb_batch_params *p, olb_batch **out) {
         return bfail(OLB_ERR_INVALID, "warps_per_block must be 1, 2 or 4");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 256)
         return bfail(OLB_ERR_INVALID, "blocks_per_sm must be in [0, 256] (0 = occupancy limit)");
-    if (p->item_row_groups < 0 || p->item_row_groups > 64)
-        return bfail(OLB_ERR_INVALID, "item_row_groups must be in [0, 64] (0 = %d)",
-                     BATCH_ITEM_ROW_GROUPS);
+    if (p->item_passes < 0 || p->item_passes > 64)
+        return bfail(OLB_ERR_INVALID, "item_passes must be in [0, 64] (0 = %d)",
+                     BATCH_ITEM_PASSES);
     olb_batch *b = new (std::nothrow) olb_batch();
     if (!b) return bfail(OLB_ERR_NOMEM, "host allocation of the batch failed");
     b->p = *p;
-    if (b->p.item_row_groups == 0) b->p.item_row_groups = BATCH_ITEM_ROW_GROUPS;
+    if (b->p.item_passes == 0) b->p.item_passes = BATCH_ITEM_PASSES;
     b->desc_size = BDISPATCH(p->storage, batch_desc_size);
     auto bail = [&](olb_status s) {
         olb_batch_destroy(b);

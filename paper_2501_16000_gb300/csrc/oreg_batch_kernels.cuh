@@ -1,6 +1,6 @@
 // Batched stream-collide: one kernel advances many independent lattices of
 // any size by one time step, its warps striding over a flattened table of
-// warp work items (row groups of one row segment of one lattice each).  The
+// warp work items (runs of warp passes over one lattice's planes).  The
 // grid is either resident as a whole (persistent) or oversubscribed, so that
 // blocks start as earlier ones finish.
 //
@@ -27,7 +27,6 @@ template <typename C> struct BatchDesc {
     void *mem;            // population memory (A-B: two buffers back to back)
     int nx, ny, pitch;
     int eq, coll;
-    int lw;               // log2 of the lanes per row segment
     size_t plane;         // elements per plane
     size_t buf_elems;     // elements per population buffer
     long long t_base;     // lattice time when the global step counter was g_base
@@ -78,7 +77,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, BATCH_MIN_BLOCKS)
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int w = lo + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < hi; w += warps) {
-        // item: (lattice, first row, segment, row groups)
+        // item: (lattice, first vector, 0, warp passes)
         const int4 it = items[w];
         const BatchDesc<typename Storage<S>::C> &d = descs[it.x];
         if (g < d.g_base || g >= d.g_end) continue;  // warp-uniform
@@ -86,21 +85,19 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, BATCH_MIN_BLOCKS)
         T *base = static_cast<T *>(d.mem);
         CollConst<typename Storage<S>::C> kk = kc;
         kk.lam = d.lam;
-        const int rows = 32 >> d.lw;
         for (int q = 0; q < it.w; ++q) {
-            const int y0 = it.y + q * rows;
+            const int v0 = it.y + q * 32;
             if constexpr (KIND == BATCH_AB) {
                 const T *src = base + (size_t)(t & 1) * d.buf_elems;
                 T *dst = base + (size_t)((t + 1) & 1) * d.buf_elems;
-                item_ab<S, EQ, COLL, S == ST_F32, WALLS>(src, dst, d.nx, d.ny, d.pitch, d.plane, y0,
-                                                         it.z, lane, d.lw, kk, t, d.sr != 0);
+                item_ab<S, EQ, COLL, S == ST_F32, WALLS>(src, dst, d.nx, d.ny, d.pitch, d.plane, v0,
+                                                         lane, kk, t, d.sr != 0);
             } else if constexpr (KIND == BATCH_AA_ODD) {
-                item_aa_odd<S, EQ, COLL, S == ST_F32, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, y0,
-                                                             it.z, lane, d.lw, kk, t, d.sr != 0);
+                item_aa_odd<S, EQ, COLL, S == ST_F32, WALLS>(base, d.nx, d.ny, d.pitch, d.plane, v0,
+                                                             lane, kk, t, d.sr != 0);
             } else {
                 item_aa_even<S, EQ, COLL, S == ST_F32, WALLS>(base, d.nx, d.ny, d.pitch, d.plane,
-                                                              y0, it.z, lane, d.lw, kk, t,
-                                                              d.sr != 0);
+                                                              v0, lane, kk, t, d.sr != 0);
             }
         }
     }

@@ -6,7 +6,7 @@
 //     (Eq. 15) equilibrium, the OReg projection (Eq. 6) and the update of
 //     Eq. 7, or lattice BGK (Eq. 1), all written in deviation variables so
 //     that no O(1) quantity is formed and then cancelled in low precision.
-//   * Warp-level shifted row-segment loads (pull streaming) and stores (push
+//   * Warp-level shifted row loads (pull streaming) and stores (push
 //     streaming of the in-place AA layout) on 16-byte vectors.
 #pragma once
 
@@ -533,14 +533,17 @@ __device__ __forceinline__ void collide(const C g[9], C post[9], const CollConst
 }
 
 // ---------------------------------------------------------------------------
-// Warp-level shifted row-segment access.
+// Warp-level shifted row access.
 //
-// A warp is split into 32/W segments of W lanes (W a power of two chosen
-// from the lattice width); each segment owns W*V consecutive nodes of one
-// row, x = xb .. xb+V-1 per lane (xb = seg*W*V + sub*V, sub = lane mod W).
-// Row storage has a pitch that is a multiple of V, so a lane's V elements are
-// one aligned 16-byte vector.  Shuffles run within the segment (width W).
-// Lanes with xb >= nx are idle but still take part in the shuffles.
+// Each lane owns V consecutive nodes x = xb .. xb+V-1 of one row.  Row
+// storage has a pitch that is a multiple of V, so a lane's V elements are one
+// aligned 16-byte vector.  Shuffles run within groups of W lanes (sub = the
+// lane's index in its group) whose vectors are consecutive within a row, except
+// where a row begins (xb = 0) or ends (xb + V >= nx): there the neighbour
+// comes from memory (halo and wrap elements).  The stream-collide kernels use
+// one group of 32 lanes holding 32 consecutive vectors of a plane in
+// row-major order, which may span rows.  Lanes with xb >= nx are idle but
+// still take part in the shuffles.
 // ---------------------------------------------------------------------------
 
 // Pull, in two phases so that a warp has all nine row fetches in flight

@@ -261,23 +261,44 @@ __device__ __forceinline__ bool lane_has_wall(int xb, int nx) {
     return xb < nx && (xb == 0 || xb + Storage<S>::V > nx - 1);
 }
 
-// One warp work item: row y, segment seg (32*V nodes) of a lattice.
+// The nodes of a lane in a warp pass.  A plane is pitch / V vectors per row,
+// rows back to back (the pitch is nx rounded up to V), and a warp pass covers
+// the 32 consecutive vectors v0 .. v0 + 31 of it in row-major order, so that
+// its loads and stores are contiguous whatever the width; the lane holds
+// vector v0 + lane: row y, nodes xb .. xb + V - 1.  Lanes past the last
+// vector are idle (xb = nx) but still take part in the shuffles.  The
+// shuffles run over the whole warp (W = 32, sub = lane); a lane whose
+// neighbour lane holds another row (xb = 0, or its vector ends the row) takes
+// the halo and wrap elements from memory instead.
+template <int S>
+__device__ __forceinline__ void lane_nodes(int v0, int lane, int nx, int ny, int pitch, int &y,
+                                           int &xb) {
+    constexpr unsigned V = Storage<S>::V;
+    const unsigned vpr = (unsigned)pitch / V, v = (unsigned)(v0 + lane);
+    const unsigned row = v / vpr;
+    if (row >= (unsigned)ny) {
+        y = ny - 1;
+        xb = nx;
+    } else {
+        y = (int)row;
+        xb = (int)((v - row * vpr) * V);
+    }
+}
+
+// One warp pass of the A-B step: vectors v0 .. v0 + 31 of a lattice's planes.
 template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict__ src,
                                         typename Storage<S>::T *__restrict__ dst, int nx, int ny,
-                                        int pitch, size_t plane, int y0, int seg, int lane, int lw,
+                                        int pitch, size_t plane, int v0, int lane,
                                         const CollConst<typename Storage<S>::C> &k, long long t,
                                         bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int W = 1 << lw, sub = lane & (W - 1);
-    int y = y0 + (lane >> lw);
-    int xb = seg * W * V + sub * V;
-    if (y >= ny) {  // rows past the lattice: idle lanes that still shuffle
-        y = ny - 1;
-        xb = nx;
-    }
+    constexpr int W = 32;
+    const int sub = lane;
+    int y, xb;
+    lane_nodes<S>(v0, lane, nx, ny, pitch, y, xb);
 
     C f[9][V];
     pull_all<S, false>(src, plane, pitch, y, ny, xb, nx, sub, W, f);
@@ -303,20 +324,18 @@ __device__ __forceinline__ void item_ab(const typename Storage<S>::T *__restrict
     }
 }
 
-// One warp per work item (a row group of one segment); the grid covers them all.
+// One warp per warp pass; the grid covers them all.
 #define OREG_AB_BODY                                                                        \
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  \
-    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);                                   \
-    if (item >= (long long)groups * segs) return; /* warp-uniform */                        \
-    item_ab<S, EQ, COLL, EXACT, WALLS>(src, dst, nx, ny, pitch, plane,                        \
-                                      (int)(item / segs) << (5 - lw), (int)(item % segs),   \
-                                      threadIdx.x & 31, lw, k, t, sr);
+    const int pass = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);                   \
+    if (pass >= passes) return; /* warp-uniform */                                          \
+    item_ab<S, EQ, COLL, EXACT, WALLS>(src, dst, nx, ny, pitch, plane, pass << 5,             \
+                                      threadIdx.x & 31, k, t, sr);
 
 template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_ab(const typename Storage<S>::T *__restrict__ src,
                                                  typename Storage<S>::T *__restrict__ dst, int nx,
-                                                 int ny, int pitch, size_t plane, int segs,
-                                                 int lw, const CollConst<typename Storage<S>::C> k,
+                                                 int ny, int pitch, size_t plane, int passes,
+                                                 const CollConst<typename Storage<S>::C> k,
                                                  long long t, bool sr) {
     OREG_AB_BODY
 }
@@ -334,7 +353,7 @@ template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(AB_CAPPED_MAX_THREADS, 5)
     k_step_ab_capped(const typename Storage<S>::T *__restrict__ src,
                      typename Storage<S>::T *__restrict__ dst, int nx, int ny, int pitch,
-                     size_t plane, int segs, int lw, const CollConst<typename Storage<S>::C> k,
+                     size_t plane, int passes, const CollConst<typename Storage<S>::C> k,
                      long long t, bool sr) {
     OREG_AB_BODY
 }
@@ -349,19 +368,14 @@ __global__ void __launch_bounds__(AB_CAPPED_MAX_THREADS, 5)
 // ---------------------------------------------------------------------------
 template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, int ny, int pitch,
-                                             size_t plane, int y0, int seg, int lane, int lw,
+                                             size_t plane, int v0, int lane,
                                              const CollConst<typename Storage<S>::C> &k,
                                              long long t, bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int W = 1 << lw, sub = lane & (W - 1);
-    int y = y0 + (lane >> lw);
-    int xb = seg * W * V + sub * V;
-    if (y >= ny) {  // rows past the lattice: idle lanes that still shuffle
-        y = ny - 1;
-        xb = nx;
-    }
+    int y, xb;
+    lane_nodes<S>(v0, lane, nx, ny, pitch, y, xb);
     if (xb >= nx) return;  // no shuffles in the even step
     typename ST::T *row = A + (size_t)y * pitch + xb;
     C f[9][V];
@@ -390,15 +404,13 @@ __device__ __forceinline__ void item_aa_even(typename Storage<S>::T *A, int nx, 
 
 template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_aa_even(typename Storage<S>::T *A, int nx, int ny,
-                                                      int pitch, size_t plane, int segs, int lw,
+                                                      int pitch, size_t plane, int passes,
                                                       const CollConst<typename Storage<S>::C> k,
                                                       long long t, bool sr) {
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);
-    if (item >= (long long)groups * segs) return;
-    item_aa_even<S, EQ, COLL, EXACT, WALLS>(A, nx, ny, pitch, plane,
-                                           (int)(item / segs) << (5 - lw), (int)(item % segs),
-                                           threadIdx.x & 31, lw, k, t, sr);
+    const int pass = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (pass >= passes) return;
+    item_aa_even<S, EQ, COLL, EXACT, WALLS>(A, nx, ny, pitch, plane, pass << 5, threadIdx.x & 31,
+                                           k, t, sr);
 }
 
 template <int S, int I>
@@ -411,19 +423,16 @@ __device__ __forceinline__ void push_plane(typename Storage<S>::T *A, size_t pla
 
 template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, int ny, int pitch,
-                                            size_t plane, int y0, int seg, int lane, int lw,
+                                            size_t plane, int v0, int lane,
                                             const CollConst<typename Storage<S>::C> &k,
                                             long long t, bool sr) {
     using ST = Storage<S>;
     using C = typename ST::C;
     constexpr int V = ST::V;
-    const int W = 1 << lw, sub = lane & (W - 1);
-    int y = y0 + (lane >> lw);
-    int xb = seg * W * V + sub * V;
-    if (y >= ny) {  // rows past the lattice: idle lanes that still shuffle
-        y = ny - 1;
-        xb = nx;
-    }
+    constexpr int W = 32;
+    const int sub = lane;
+    int y, xb;
+    lane_nodes<S>(v0, lane, nx, ny, pitch, y, xb);
 
     C f[9][V];
     pull_all<S, true>(A, plane, pitch, y, ny, xb, nx, sub, W, f);
@@ -449,16 +458,14 @@ __device__ __forceinline__ void item_aa_odd(typename Storage<S>::T *A, int nx, i
 }
 
 #define OREG_AA_ODD_BODY                                                                    \
-    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  \
-    const int groups = (ny + (32 >> lw) - 1) >> (5 - lw);                                   \
-    if (item >= (long long)groups * segs) return;                                           \
-    item_aa_odd<S, EQ, COLL, EXACT, WALLS>(A, nx, ny, pitch, plane,                          \
-                                          (int)(item / segs) << (5 - lw), (int)(item % segs), \
-                                          threadIdx.x & 31, lw, k, t, sr);
+    const int pass = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);                   \
+    if (pass >= passes) return;                                                             \
+    item_aa_odd<S, EQ, COLL, EXACT, WALLS>(A, nx, ny, pitch, plane, pass << 5,                \
+                                          threadIdx.x & 31, k, t, sr);
 
 template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, int nx, int ny,
-                                                     int pitch, size_t plane, int segs, int lw,
+                                                     int pitch, size_t plane, int passes,
                                                      const CollConst<typename Storage<S>::C> k,
                                                      long long t, bool sr) {
     OREG_AA_ODD_BODY
@@ -466,7 +473,7 @@ __global__ void __launch_bounds__(256) k_step_aa_odd(typename Storage<S>::T *A, 
 template <int S, int EQ, int COLL, bool EXACT, bool WALLS>
 __global__ void __launch_bounds__(256, step_min_blocks(S))
     k_step_aa_odd_capped(typename Storage<S>::T *A, int nx, int ny, int pitch, size_t plane,
-                         int segs, int lw, const CollConst<typename Storage<S>::C> k, long long t,
+                         int passes, const CollConst<typename Storage<S>::C> k, long long t,
                          bool sr) {
     OREG_AA_ODD_BODY
 }
@@ -483,31 +490,31 @@ template <int S> struct StepLaunch {
     template <int EQ, int COLL, bool EXACT, bool WALLS>
     static void step_eq(const StepArgs &a, dim3 grid, dim3 block) {
         const CollConst<C> &k = *static_cast<const CollConst<C> *>(a.kconst);
-        const int segs = a.segs;
+        const int passes = a.passes;
         if (a.layout == 0) {
             if constexpr (ab_capped<S, EQ, WALLS>()) {
                 if (block.x <= (unsigned)AB_CAPPED_MAX_THREADS) {
                     k_step_ab_capped<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
                         static_cast<const T *>(a.src), static_cast<T *>(a.dst), a.nx, a.ny,
-                        a.pitch, a.plane, segs, a.lw, k, a.t, a.sr != 0);
+                        a.pitch, a.plane, passes, k, a.t, a.sr != 0);
                     return;
                 }
             }
             k_step_ab<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
                 static_cast<const T *>(a.src), static_cast<T *>(a.dst), a.nx, a.ny, a.pitch,
-                a.plane, segs, a.lw, k, a.t, a.sr != 0);
+                a.plane, passes, k, a.t, a.sr != 0);
         } else if (a.parity == 0) {
             k_step_aa_even<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
-                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
+                static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, passes, k, a.t,
                 a.sr != 0);
         } else {
             if constexpr (aa_odd_capped<S, EQ, WALLS>()) {
                 k_step_aa_odd_capped<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
-                    static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
+                    static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, passes, k, a.t,
                     a.sr != 0);
             } else {
                 k_step_aa_odd<S, EQ, COLL, EXACT, WALLS><<<grid, block, 0, a.stream>>>(
-                    static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, segs, a.lw, k, a.t,
+                    static_cast<T *>(a.src), a.nx, a.ny, a.pitch, a.plane, passes, k, a.t,
                     a.sr != 0);
             }
         }
@@ -541,10 +548,8 @@ template <int S> struct StepLaunch {
 
     static cudaError_t step(const StepArgs &a) {
         const int warps = a.warps_per_block;
-        const long long groups = (a.ny + (32 >> a.lw) - 1) >> (5 - a.lw);
-        const long long items = groups * a.segs;
         dim3 block(32 * warps);
-        dim3 grid((unsigned)((items + warps - 1) / warps));
+        dim3 grid((unsigned)((a.passes + warps - 1) / warps));
         if (a.walls) step_walls<true>(a, grid, block);
         else step_walls<false>(a, grid, block);
         return cudaGetLastError();

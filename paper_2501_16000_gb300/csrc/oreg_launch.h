@@ -26,8 +26,7 @@ struct StepArgs {
     void *dst;         // A-B: buffer of S_{t+1}; AA: unused
     int nx, ny, pitch;
     size_t plane;
-    int segs;          // row segments of W*V nodes per row
-    int lw;            // log2 of W, the lanes per row segment (W <= 32)
+    int passes;        // warp passes over a plane (warp_passes)
     int eq, coll, layout, parity;  // eq: kernel equilibrium kind (EQ_GUIDED_LOCAL for
                                    // the guided equilibrium at the local temperature)
     int comp;          // exact conserved-moment sums (FP32 only)
@@ -39,23 +38,13 @@ struct StepArgs {
     cudaStream_t stream;
 };
 
-// Lanes per row segment for an nx x ny lattice, as log2: a warp pass covers
-// 32/W rows of one W-lane segment of W*V nodes, and W (a power of two <= 32)
-// is the one that needs the fewest passes, i.e. leaves the fewest lanes idle
-// on partial segments and partial row groups; among equal counts the widest
-// (fewest segment-edge halo loads).  Every W gives bitwise the same results.
-inline int segment_log2(int nx, int ny, int V) {
-    int best = 5;
-    long long best_passes = -1;
-    for (int lw = 5; lw >= 0; --lw) {
-        const long long seg = (long long)V << lw, rows = 32 >> lw;
-        const long long passes = ((nx + seg - 1) / seg) * ((ny + rows - 1) / rows);
-        if (best_passes < 0 || passes < best_passes) {
-            best = lw;
-            best_passes = passes;
-        }
-    }
-    return best;
+// Warp passes of the stream-collide kernels over a plane of ny rows of
+// `pitch` elements (pitch a multiple of V): a pass covers 32 consecutive
+// vectors of V elements in row-major order, rows back to back, so only the
+// last pass of a lattice has idle lanes.  Every vector index of a plane fits
+// an int (checked when a lattice is created).
+inline long long warp_passes(int pitch, int ny, int V) {
+    return ((long long)(pitch / V) * ny + 31) / 32;
 }
 
 enum { INIT_SHEAR = 0, INIT_SHOCK = 1, INIT_FIELDS = 2 };
@@ -108,11 +97,10 @@ OREG_DECLARE_LAUNCHERS(bf16)
 cudaError_t step_f32c64(const StepArgs &a);
 
 // One launch of the batched stream-collide kernel (see oreg_batch_kernels.cuh).
-// Default row groups (32/W rows of one W-lane segment each) per batched work
-// item: a warp takes up to this many consecutive row groups of one lattice
-// segment, reading the lattice's descriptor once (olb_batch_params.
-// item_row_groups overrides it).
-constexpr int BATCH_ITEM_ROW_GROUPS = 4;
+// Default warp passes (32 consecutive vectors each) per batched work item: a
+// warp takes up to this many consecutive passes over one lattice, reading the
+// lattice's descriptor once (olb_batch_params.item_passes overrides it).
+constexpr int BATCH_ITEM_PASSES = 4;
 
 // One slot of a batch: a (walls, equilibrium kind, collision) kernel and the
 // collision constants of one class of lattices (all but 1 - 1/tau).
@@ -123,7 +111,7 @@ struct BatchSlot {
 
 struct BatchLaunch {
     const void *descs;        // BatchDesc<C>[]
-    const int4 *items;        // work items (descriptor, first row, segment), grouped
+    const int4 *items;        // work items (descriptor, first vector, 0, passes), grouped
     const int *groups;        // device: item offsets of the (slot, parity) groups
     const long long *g;       // device: global step counter of this round
     int k;                    // step within the round

@@ -33,7 +33,7 @@ import time
 
 import numpy as np
 
-from .batch import ITEM_ROW_GROUPS, BatchEngine, work_items
+from .batch import ITEM_PASSES, BatchEngine, work_items
 from .engine import Lattice, required_bytes
 
 
@@ -85,7 +85,7 @@ def _bytes(lat_case, storage, layout):
 class Server:
     def __init__(self, storage="f16", layout="ab", budget_bytes=120e9, steps_per_launch=100,
                  max_lattices=8192, max_items=1 << 24, warps_per_block=4, blocks_per_sm=0,
-                 keep_fields=True, engine=None, item_row_groups=ITEM_ROW_GROUPS):
+                 keep_fields=True, engine=None, item_passes=ITEM_PASSES):
         """``engine`` replaces the BatchEngine (anything with its new_lattice,
         add, remove, remaining, run, record_event, read_back and close
         methods)."""
@@ -95,8 +95,8 @@ class Server:
         self.engine = engine if engine is not None else BatchEngine(
             storage, layout, max_lattices=max_lattices, max_items=max_items,
             steps_per_launch=steps_per_launch, warps_per_block=warps_per_block,
-            blocks_per_sm=blocks_per_sm, item_row_groups=item_row_groups)
-        self.item_row_groups = int(item_row_groups)
+            blocks_per_sm=blocks_per_sm, item_passes=item_passes)
+        self.item_passes = int(item_passes)
         self.max_items = max_items
         self.rounds = 0
         self.peak_bytes = 0
@@ -180,7 +180,7 @@ class Server:
                     req = queue[0]
                     need = self.request_bytes(req.lattice)
                     items = work_items(req.lattice.nx, req.lattice.ny, self.storage,
-                                       self.item_row_groups)
+                                       self.item_passes)
                     if need > self.budget:
                         raise ValueError(f"request {req.rid} needs {need} B > budget")
                     if in_bytes + need > self.budget or in_items + items > self.max_items:

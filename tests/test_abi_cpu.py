@@ -46,7 +46,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.olb_abi_version() == 4
+    assert lib.olb_abi_version() == 5
 
 
 def _params(**kw):
@@ -68,7 +68,8 @@ def test_required_bytes(lib, storage, layout, elem, nbuf):
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(ny=-1), dict(tau=0.5), dict(tau=float("nan")), dict(rho0=0.0),
     dict(theta=0.0), dict(theta=1.0), dict(eq="poly2", theta=0.3),
-    dict(nx=1 << 20, ny=1 << 17)])   # 2^37 nodes: beyond the 2^36 limit (no size_t overflow)
+    dict(nx=1 << 20, ny=1 << 17),    # 2^37 nodes: beyond the 2^36 limit (no size_t overflow)
+    dict(nx=200000, ny=200000, storage="f64")])   # 2e10 > 2^31 vectors per plane
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     p = _params(**bad)
     assert lib.olb_required_bytes(ctypes.byref(p)) == 0

@@ -99,7 +99,7 @@ def test_batch_membership_rules():
             other = Lattice(64, 8, 0.8, storage="f32", layout="ab", stream=eng.stream)
             eng.add(other, 1)
         other.close()
-        # 256 x 400 f16: 400 row groups of one segment, 100 items of 4 groups > 64
+        # 256 x 400 f16: 400 warp passes, 100 items of 4 passes > 64
         big = eng.new_lattice(W.LatticeCase(nx=256, ny=400, tau=0.8, case="shock", x_split=10))
         with pytest.raises(B.OregError) as e:      # work-item capacity
             eng.add(big, 1)

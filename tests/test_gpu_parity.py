@@ -306,7 +306,7 @@ def test_failed_allocation_is_reported_and_harmless():
     from paper_2501_16000_gb300 import binding as B
     from paper_2501_16000_gb300.engine import make_params
     lib = B.load()
-    p = make_params(nx=200000, ny=200000, tau=0.8, storage="f64")      # ~5.8 TB of populations
+    p = make_params(nx=60000, ny=60000, tau=0.8, storage="f64")        # ~518 GB of populations
     h = ctypes.c_void_p()
     assert lib.olb_create_lattice(ctypes.byref(p), ctypes.byref(h)) == B.OLB_ERR_NOMEM
     assert "allocating" in lib.olb_last_error().decode()

@@ -9,7 +9,7 @@ import pytest
 
 from paper_2501_16000_gb300 import workloads as W
 from paper_2501_16000_gb300.analysis import fit_decay
-from paper_2501_16000_gb300.batch import segment_lanes, work_items
+from paper_2501_16000_gb300.batch import warp_passes, work_items
 from paper_2501_16000_gb300.engine import required_bytes
 
 
@@ -56,23 +56,28 @@ def test_fit_decay_recovers_an_exponential():
 
 
 @pytest.mark.parametrize("storage,v", [("f64", 2), ("f32", 4), ("f16", 8)])
-def test_work_items_cover_every_node_once(storage, v):
-    for nx in (1, 5, 33, 37, 100, 256, 257, 300, 1024, 3000, 8192):
-        for ny in (1, 3, 4, 32, 33, 500, 8192):
-            w = segment_lanes(nx, ny, v)
-            passes = {u: math.ceil(nx / (u * v)) * math.ceil(ny / (32 // u))
-                      for u in (1, 2, 4, 8, 16, 32)}
-            # fewest warp passes, the widest segment among equals
-            assert passes[w] == min(passes.values())
-            assert all(u <= w for u in passes if passes[u] == passes[w])
-            groups = math.ceil(ny / (32 // w))
-            assert work_items(nx, ny, storage) * 4 * 32 * v >= nx * ny
-            assert work_items(nx, ny, storage) == math.ceil(groups / 4) * math.ceil(nx / (w * v))
-    # full-width segments where nothing idles (the benchmark lattice), narrower
-    # segments where a 32-lane one would leave lanes idle
-    assert segment_lanes(8192, 8192, v) == 32
-    assert segment_lanes(2048, 4, 4) == 32
-    assert segment_lanes(300, 500, 8) == 2 and segment_lanes(33, 500, 8) == 1
+def test_warp_passes_cover_every_node_once(storage, v):
+    """The stream-collide kernels' lane mapping, restated: warp pass p, lane l
+    holds vector 32 p + l of the row-major planes (rows of ceil(nx / v)
+    vectors), i.e. row y = vector // vpr and nodes xb .. xb + v - 1 with
+    xb = v (vector % vpr); lanes past the last vector idle.  Every node is
+    held by exactly one lane, and only the last pass has idle lanes."""
+    for nx in (1, 5, 33, 37, 100, 256, 257, 300, 1024, 3000):
+        for ny in (1, 3, 4, 32, 33, 500):
+            vpr = math.ceil(nx / v)
+            passes = warp_passes(nx, ny, v)
+            vec = np.arange(passes * 32)
+            y, xb = vec // vpr, (vec % vpr) * v
+            live = y < ny
+            assert (~live).sum() < 32 and live[: (passes - 1) * 32].all()
+            held = np.zeros((ny, nx), dtype=int)
+            for j in range(v):
+                ok = live & (xb + j < nx)
+                np.add.at(held, (y[ok], xb[ok] + j), 1)
+            assert (held == 1).all()
+            for r in (1, 2, 4, 8):
+                assert work_items(nx, ny, storage, r) == math.ceil(passes / r)
+    assert warp_passes(8192, 8192, 8) == 8192 * 8192 // 256
 
 
 class _FakeLattice:
@@ -252,7 +257,7 @@ def test_autotune_picks_the_fastest_candidate_and_honours_the_cache(tmp_path):
         c += {"ab": 0.0, "aa": 0.3}[cfg["layout"]]
         c += {1: 0.2, 2: 0.05, 4: 0.0}[cfg["warps_per_block"]]
         c += {0: 0.0, 2: 0.1, 32: 0.03, 64: 0.2, 128: 0.4}[cfg["blocks_per_sm"]]
-        c += {1: 0.08, 2: 0.0, 4: 0.02, 8: 0.05}[cfg["item_row_groups"]]
+        c += {1: 0.08, 2: 0.0, 4: 0.02, 8: 0.05}[cfg["item_passes"]]
         c += {25: 0.04, 50: 0.02, 100: 0.0, 200: 0.01}[cfg["steps_per_launch"]]
         return c
 
@@ -264,7 +269,7 @@ def test_autotune_picks_the_fastest_candidate_and_honours_the_cache(tmp_path):
     path = str(tmp_path / "tune.json")
     r = BT.autotune(cases, "f16", repeats=3, cache_path=path, measure=measure)
     assert (r["layout"], r["warps_per_block"], r["blocks_per_sm"]) == ("ab", 4, 0)
-    assert (r["item_row_groups"], r["steps_per_launch"]) == (2, 100)
+    assert (r["item_passes"], r["steps_per_launch"]) == (2, 100)
     assert abs(r["ms_per_step"] - 1.0) < 1e-12
     idents = [tuple(sorted(c.items())) for c in calls]
     assert len(idents) == len(set(idents)) == r["candidates"]
