@@ -176,8 +176,8 @@ def size_class(cases) -> str:
 # then steps per graph replay.  Blocks per SM above the resident count (0)
 # oversubscribe the grid: its warps still stride over the work items, but
 # blocks start as earlier ones finish, so the block scheduler evens out a mix
-# of uneven items (on the 512-lattice FP16 mix: 121 GLUPS with every block
-# resident, 126 with 64 blocks per SM and 4 warp passes per item).
+# of uneven items (on the 512-lattice FP16 mix: 136 GLUPS with every block
+# resident, 142 with 64 blocks per SM, 4 warp passes per item).
 TUNE_STAGES = (
     {"layout": ("ab", "aa"), "warps_per_block": (1, 2, 4), "blocks_per_sm": (0, 2, 32, 64, 128)},
     {"item_passes": (1, 2, 4, 8)},
