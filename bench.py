@@ -546,12 +546,18 @@ def batched_section(args):
                 "median": float(f"{np.median(e):.3e}"), "le_1e-4": int((e <= 1e-4).sum())}
 
     r32 = routed["f32"]
+    peak, peak_kind = measured_peaks()
+    gbs = nodes * steps * 36 / dt / 1e9                      # FP16: 9 reads + 9 writes x 2 B
     return {
         "workload": f"{len(cases)} lattices, sides log-uniform [32,1024] (seed 1), tau U[0.51,1], "
                     f"u0 U[0.01,0.1], shear/shock 50/50, {steps} steps each, FP16 storage "
                     f"(stochastic rounding) / FP32 compute, graph replay per {K} steps",
         "nodes": nodes, "solves_per_s": round(len(cases) / dt, 2), "seconds": round(dt, 4),
         "mlups": round(nodes * steps / dt / 1e6, 1), "tuned": tuned,
+        "roofline": {"bound": "hbm", "bytes_per_node": 36, "achieved": round(gbs, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(gbs / peak, 4),
+                     "note": "whole solve (wall clock, graph replays included) x 36 B per node-step"},
         "tune_seconds": round(t_tune, 1),
         "routed": {"rule": "shear waves with 1/(u0 sqrt(N) gamma T) > 0.12 in FP32 storage",
                    "fp32_lattices": len(r32),
