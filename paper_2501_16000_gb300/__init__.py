@@ -3,7 +3,7 @@
 The compute path is the CUDA library ``liboreg.so`` built from ``csrc/``;
 ``binding`` is its thin ctypes binding (same names as the C ABI in
 ``include/oreg.h``), ``engine`` holds the ``Lattice`` wrapper, ``batch`` the
-batched persistent path and ``serve`` the continuous-batching request loop.
+batched path and ``serve`` the continuous-batching request loop.
 ``workloads`` holds only seeded input generators.
 
 Importing the package loads nothing; the library is opened on first use and a
