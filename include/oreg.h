@@ -298,7 +298,8 @@ olb_status olb_wave_mode(olb_lattice *lat, int32_t m, int32_t n, double *a_sin,
  * slots of one kernel (walls, equilibrium kind, collision) and one class of
  * collision constants (the same theta, rho0 and equilibrium; tau is per
  * member), and every step launches one kernel per slot, whose class constants
- * are a launch parameter.  Joining and leaving rewrite the device tables
+ * are a launch parameter; within the graph the kernels of different slots
+ * run side by side (each slot's steps in order).  Joining and leaving rewrite the device tables
  * only; the graph is captured again when a member brings a new slot (at most
  * 64 slots are in use at a time: olb_batch_add returns OLB_ERR_NOMEM beyond).
  * A member is advanced exactly the number of steps it was added with, then

@@ -52,6 +52,7 @@ olb_status bcuda(cudaError_t e, const char *what) {
 // compacts its slot list; work-item groups are (slot, parity class).
 constexpr int MAX_SLOTS = 64;
 constexpr int NGROUPS = 2 * MAX_SLOTS;
+constexpr int SIDE_STREAMS = 8;  // capture streams for the slots of a step
 
 // (walls, equilibrium kind, collision) of a lattice: its batch kernel
 int combo_index(const olb_lattice *L) {
@@ -144,6 +145,13 @@ struct olb_batch {
     int graph_slots;        // slots the captured graph launches
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    // Used while capturing only: with several slots, each slot's launches go
+    // to one of these streams, forked from and joined back into the batch
+    // stream, so that the graph runs the kernels of different slots (disjoint
+    // lattices) side by side instead of one after another.
+    cudaStream_t side[SIDE_STREAMS];
+    cudaEvent_t fork_ev, join_ev[SIDE_STREAMS];
+    int nside;              // side streams created so far
 };
 
 namespace {
@@ -253,9 +261,38 @@ olb_status upload(olb_batch *b) {
 
 __global__ void k_batch_advance(long long *g, int K) { *g += K; }
 
+// The side streams (and their events) of a capture over nside of them.
+olb_status ensure_side(olb_batch *b, int nside) {
+    if (!b->fork_ev)
+        B_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming), "creating capture events");
+    while (b->nside < nside) {
+        const int i = b->nside;
+        B_CUDA(cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking), "creating a capture stream");
+        const cudaError_t e = cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(b->side[i]);
+            b->side[i] = nullptr;
+            return bcuda(e, "creating capture events");
+        }
+        ++b->nside;
+    }
+    return OLB_OK;
+}
+
+// Captures one round: K steps of every slot, then the counter increment.
+// With one slot its launches stay on the batch stream; with several, slot s
+// goes to side stream s mod S (S = min(slots, SIDE_STREAMS)), forked from the
+// batch stream before the first step and joined back before the increment,
+// so each slot's steps stay in order while different slots overlap.
 olb_status capture(olb_batch *b) {
     std::vector<BatchSlot> slots(b->slots.size());
     for (size_t s = 0; s < b->slots.size(); ++s) slots[s] = BatchSlot{b->slots[s].combo, b->slots[s].k.data()};
+    const int nslots = (int)slots.size();
+    const int nside = nslots > 1 ? std::min(nslots, SIDE_STREAMS) : 0;
+    if (nside) {
+        const olb_status st = ensure_side(b, nside);
+        if (st != OLB_OK) return st;
+    }
     BatchLaunch a{};
     a.descs = b->d_descs;
     a.items = b->d_items;
@@ -264,15 +301,40 @@ olb_status capture(olb_batch *b) {
     a.layout = b->p.layout;
     a.grid = b->grid;
     a.block = b->block;
-    a.stream = b->stream;
-    a.nslots = (int)slots.size();
     a.slots = slots.data();
     B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
            "beginning graph capture");
     cudaError_t e = cudaSuccess;
+    int forked = 0;  // side streams that joined the capture
+    if (nside) {
+        e = cudaEventRecord(b->fork_ev, b->stream);
+        while (forked < nside && e == cudaSuccess) {
+            e = cudaStreamWaitEvent(b->side[forked], b->fork_ev, 0);
+            if (e == cudaSuccess) ++forked;
+        }
+    }
     for (int k = 0; k < b->p.steps_per_launch && e == cudaSuccess; ++k) {
         a.k = k;
-        e = BDISPATCH(b->p.storage, batch_step, a);
+        if (!nside) {
+            a.first_slot = 0;
+            a.nslots = nslots;
+            a.stream = b->stream;
+            e = BDISPATCH(b->p.storage, batch_step, a);
+        } else {
+            for (int s = 0; s < nslots && e == cudaSuccess; ++s) {
+                a.first_slot = s;
+                a.nslots = 1;
+                a.stream = b->side[s % nside];
+                e = BDISPATCH(b->p.storage, batch_step, a);
+            }
+        }
+    }
+    // join every side stream that joined the capture (also after an error,
+    // so that the capture can end)
+    for (int i = 0; i < forked; ++i) {
+        cudaError_t ej = cudaEventRecord(b->join_ev[i], b->side[i]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(b->stream, b->join_ev[i], 0);
+        if (e == cudaSuccess) e = ej;
     }
     if (e == cudaSuccess) {
         k_batch_advance<<<1, 1, 0, b->stream>>>(b->d_g, b->p.steps_per_launch);
@@ -288,7 +350,7 @@ olb_status capture(olb_batch *b) {
     b->graph = g;
     B_CUDA(cudaGraphInstantiate(&b->exec, g, 0), "instantiating batch graph");
     b->captured = true;
-    b->graph_slots = a.nslots;
+    b->graph_slots = nslots;
     return OLB_OK;
 }
 
@@ -468,6 +530,11 @@ olb_status olb_batch_destroy(olb_batch *b) {
         if (b->h_stage[s]) cudaFreeHost(b->h_stage[s]);
         if (b->stage_done[s]) cudaEventDestroy(b->stage_done[s]);
     }
+    for (int i = 0; i < b->nside; ++i) {
+        cudaStreamDestroy(b->side[i]);
+        cudaEventDestroy(b->join_ev[i]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return st;

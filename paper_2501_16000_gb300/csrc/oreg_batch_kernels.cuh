@@ -126,7 +126,7 @@ template <int S> struct BatchLaunchT {
     // combo = (walls * 3 + eq) * 2 + coll
     template <int KIND>
     static cudaError_t launch_kind(const BatchLaunch &a) {
-        for (int s = 0; s < a.nslots; ++s) {
+        for (int s = a.first_slot; s < a.first_slot + a.nslots; ++s) {
             const int combo = a.slots[s].combo;
             const int coll = combo & 1, eq = (combo >> 1) % 3, walls = combo / 6;
             if (walls) launch_eq<KIND, true>(a, s, eq, coll);

@@ -116,8 +116,9 @@ struct BatchLaunch {
     const long long *g;       // device: global step counter of this round
     int k;                    // step within the round
     int layout;
-    int nslots;               // slots to launch, one kernel each per step
-    const BatchSlot *slots;
+    int first_slot, nslots;   // slots to launch (first_slot .. first_slot + nslots - 1),
+                              // one kernel each per step
+    const BatchSlot *slots;   // every slot of the batch (indexed by slot)
     int grid, block;
     cudaStream_t stream;
 };

@@ -66,6 +66,36 @@ def test_batch_equals_alone_bitwise(storage, layout, blocks):
             assert np.array_equal(ref.populations(), got[j]), (j, c)
 
 
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_many_slots_overlap_and_stay_bitwise(layout):
+    """Ten constant classes (theta 0.30 .. 0.39, alternating OReg and BGK), more
+    slots than the graph's side streams: the slots' launches run on streams
+    forked from the batch stream, two slots share a stream, and every lattice
+    still ends bitwise equal to its run alone."""
+    from paper_2501_16000_gb300.batch import BatchEngine
+    from paper_2501_16000_gb300.engine import Lattice
+    cases = [W.LatticeCase(nx=40 + 13 * j, ny=9 + 5 * j, tau=0.55 + 0.03 * j, theta=0.30 + 0.01 * j,
+                           coll="bgk" if j % 2 else "oreg", case="shear", u0=0.04, m=1, n=1)
+             for j in range(10)]
+    steps = 2 * 6 + 3
+    with BatchEngine("f16", layout, max_lattices=16, max_items=1 << 14, steps_per_launch=6,
+                     warps_per_block=4, blocks_per_sm=32) as eng:
+        lats = [eng.new_lattice(c) for c in cases]
+        for lat in lats:
+            eng.add(lat, steps)
+        eng.run(3)
+        eng.wait()
+        got = [lat.populations() for lat in lats]
+        for lat in lats:
+            assert lat.time == steps
+            lat.close()
+    for c, g in zip(cases, got):
+        with Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, "f16", layout) as ref:
+            ref.init_case(c)
+            ref.step(steps)
+            assert np.array_equal(ref.populations(), g), c
+
+
 def test_batch_fp64_matches_oracle():
     from paper_2501_16000_gb300.batch import BatchEngine
     cases = mixed_cases()[:6]
