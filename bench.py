@@ -492,7 +492,7 @@ def batched_section(args):
     import torch
     from paper_2501_16000_gb300 import workloads as W
     from paper_2501_16000_gb300.analysis import measure_decay
-    from paper_2501_16000_gb300.batch import autotune, route_storage
+    from paper_2501_16000_gb300.batch import autotune, kernel_classes, route_storage
     from paper_2501_16000_gb300.engine import Lattice
     steps = args.batch_steps
     cases = W.batch_mix(count=args.batch_count, seed=1, steps=steps)
@@ -507,6 +507,10 @@ def batched_section(args):
     t_tune = time.perf_counter() - t_tune
     K = tuned["steps_per_launch"]
     dt = _timed_batch_solve({"f16": cases}, tuned, steps)
+    # the same lattices over six kernel / constant classes (slots), tuned anew
+    classes = W.batch_mix_classes(count=args.batch_count, seed=1, steps=steps)
+    tuned_cls = tuned if args.batch_config else autotune(classes, "f16", use_cache=False)
+    dt_cls = _timed_batch_solve({"f16": classes}, tuned_cls, steps)
     route = [route_storage(c, "f16") for c in cases]
     routed = {"f16": [c for c, r in zip(cases, route) if r == "f16"],
               "f32": [c for c, r in zip(cases, route) if r == "f32"]}
@@ -559,6 +563,11 @@ def batched_section(args):
                      "frac": round(gbs / peak, 4),
                      "note": "whole solve (wall clock, graph replays included) x 36 B per node-step"},
         "tune_seconds": round(t_tune, 1),
+        "six_classes": {"workload": "the same lattices, BGK for odd j, polynomial equilibrium for odd "
+                                    "j // 2, else guided at theta 0.36 / 0.30 (workloads.batch_mix_classes)",
+                        "slots": kernel_classes(classes),
+                        "solves_per_s": round(len(classes) / dt_cls, 2),
+                        "mlups": round(nodes * steps / dt_cls / 1e6, 1), "tuned": tuned_cls},
         "routed": {"rule": "shear waves with 1/(u0 sqrt(N) gamma T) > 0.12 in FP32 storage",
                    "fp32_lattices": len(r32),
                    "fp32_node_fraction": round(sum(c.nodes for c in r32) / nodes, 4),

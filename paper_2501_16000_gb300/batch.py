@@ -165,9 +165,16 @@ def route_storage(case, storage="f16", limit=FP16_NOISE_LIMIT, steps=None) -> st
     return storage
 
 
+def kernel_classes(cases) -> int:
+    """Distinct (boundary, equilibrium, collision, temperature mode, theta,
+    rho0) combinations: the slots a batch of these lattices launches (one
+    kernel each per step)."""
+    return len({(c.boundary, c.eq, c.coll, c.theta_mode, c.theta, c.rho0) for c in cases})
+
+
 def size_class(cases) -> str:
     nodes = sum(c.nx * c.ny for c in cases)
-    return f"n{len(cases)}-2^{int(math.log2(max(nodes, 1)))}"
+    return f"n{len(cases)}-2^{int(math.log2(max(nodes, 1)))}-s{kernel_classes(cases)}"
 
 
 # Search space of the tuner.  The stages run in this order, each over one

@@ -237,6 +237,20 @@ def batch_mix(count: int = 512, seed: int = 1, lo: int = 32, hi: int = 1024,
     return out
 
 
+def batch_mix_classes(count: int = 512, seed: int = 1, steps: int = 1000) -> list[LatticeCase]:
+    """The lattices of ``batch_mix`` spread over six kernel / constant
+    classes: lattice j runs BGK for odd j (else OReg), the polynomial
+    equilibrium (theta = 1/3) when j // 2 is odd, else the guided one at
+    theta = 0.36 or 0.30 (j // 4 even or odd)."""
+    out = []
+    for j, c in enumerate(batch_mix(count, seed, steps=steps)):
+        poly = (j // 2) % 2 == 1
+        out.append(dataclasses.replace(
+            c, coll="bgk" if j % 2 else "oreg", eq="poly2" if poly else "guided",
+            theta=THETA0 if poly else (0.30 if (j // 4) % 2 else 0.36)))
+    return out
+
+
 @dataclasses.dataclass(frozen=True)
 class Request:
     """One solve request of the serving trace."""
