@@ -639,6 +639,62 @@ __device__ __forceinline__ T shfl_down_raw(T v, int d, int w) {
     }
 }
 
+// Stores of part of a lane's 16-byte vector at p (16-byte aligned), in pieces
+// aligned to their size: the elements 1 .. V-1, or the first L (0 <= L < V).
+template <int S>
+__device__ __forceinline__ void st_tail1(typename Storage<S>::T *p, const Vec<S> &v) {
+    constexpr int V = Storage<S>::V;
+    char *b = reinterpret_cast<char *>(p);
+    if constexpr (V == 2) {
+        *reinterpret_cast<uint2 *>(b + 8) = make_uint2(v.raw.z, v.raw.w);
+    } else if constexpr (V == 4) {
+        *reinterpret_cast<unsigned *>(b + 4) = v.raw.y;
+        *reinterpret_cast<uint2 *>(b + 8) = make_uint2(v.raw.z, v.raw.w);
+    } else {
+        *reinterpret_cast<unsigned short *>(b + 2) = (unsigned short)(v.raw.x >> 16);
+        *reinterpret_cast<unsigned *>(b + 4) = v.raw.y;
+        *reinterpret_cast<uint2 *>(b + 8) = make_uint2(v.raw.z, v.raw.w);
+    }
+}
+template <int S>
+__device__ __forceinline__ void st_head(typename Storage<S>::T *p, const Vec<S> &v, int L) {
+    constexpr int V = Storage<S>::V;
+    char *b = reinterpret_cast<char *>(p);
+    if constexpr (V == 2) {
+        if (L & 1) *reinterpret_cast<uint2 *>(b) = make_uint2(v.raw.x, v.raw.y);
+    } else if constexpr (V == 4) {
+        if (L & 2) *reinterpret_cast<uint2 *>(b) = make_uint2(v.raw.x, v.raw.y);
+        if (L & 1) *reinterpret_cast<unsigned *>(b + 4 * (L & 2)) = (L & 2) ? v.raw.z : v.raw.x;
+    } else {
+        if (L & 4) *reinterpret_cast<uint2 *>(b) = make_uint2(v.raw.x, v.raw.y);
+        if (L & 2) *reinterpret_cast<unsigned *>(b + 2 * (L & 4)) = (L & 4) ? v.raw.z : v.raw.x;
+        if (L & 1) {
+            const int k = L & 6;
+            const unsigned w = (k & 4) ? ((k & 2) ? v.raw.w : v.raw.z) : ((k & 2) ? v.raw.y : v.raw.x);
+            *reinterpret_cast<unsigned short *>(b + 2 * k) = (unsigned short)(w & 0xFFFFu);
+        }
+    }
+}
+// Element j (0 <= j < V) of a lane's vector, as raw bits of the element size.
+template <int S>
+__device__ __forceinline__ typename Storage<S>::T vec_elem(const Vec<S> &v, int j) {
+    constexpr int V = Storage<S>::V;
+    using T = typename Storage<S>::T;
+    T out;
+    if constexpr (V == 2) {
+        const uint2 w = (j & 1) ? make_uint2(v.raw.z, v.raw.w) : make_uint2(v.raw.x, v.raw.y);
+        memcpy(&out, &w, 8);
+    } else if constexpr (V == 4) {
+        const unsigned w = (j & 2) ? ((j & 1) ? v.raw.w : v.raw.z) : ((j & 1) ? v.raw.y : v.raw.x);
+        memcpy(&out, &w, 4);
+    } else {
+        const unsigned w = (j & 4) ? ((j & 2) ? v.raw.w : v.raw.z) : ((j & 2) ? v.raw.y : v.raw.x);
+        const unsigned short h = (unsigned short)((j & 1) ? (w >> 16) : (w & 0xFFFFu));
+        memcpy(&out, &h, 2);
+    }
+    return out;
+}
+
 // Push of already encoded elements: e[j] of node x = xb + j goes to position
 // x + CX (periodic) of the row at rowp.  Each position is written exactly
 // once, by the lane that owns the node the value comes from; positions past
@@ -664,15 +720,17 @@ __device__ __forceinline__ void store_row_shifted_raw(typename Storage<S>::T *ro
             v.e[0] = from_left;
 #pragma unroll
             for (int j = 1; j < V; ++j) v.e[j] = e[j - 1];
-            if (!(sub == 0 || xb == 0)) {
-                st_vec<S>(rowp + xb, v);
-            } else {
+            // element 0 of a lane that starts the warp or the row comes from
+            // another lane's push (the warp's neighbour, or the row's end)
+            if (!(sub == 0 || xb == 0)) st_vec<S>(rowp + xb, v);
+            else st_tail1<S>(rowp + xb, v);
+            // node nx - 1 wraps to x = 0: it is element nx - 1 - xb of v shifted by one
+            if (xb + V > nx - 1) {
+                Vec<S> o;
 #pragma unroll
-                for (int j = 1; j < V; ++j) rowp[xb + j] = v.e[j];
+                for (int j = 0; j < V; ++j) o.e[j] = e[j];
+                rowp[0] = vec_elem<S>(o, nx - 1 - xb);
             }
-#pragma unroll
-            for (int j = 0; j < V; ++j)
-                if (xb + j == nx - 1) rowp[0] = e[j];
             if (sub == W - 1 && xb + V < nx) rowp[xb + V] = e[V - 1];
         }
     } else {
@@ -682,18 +740,13 @@ __device__ __forceinline__ void store_row_shifted_raw(typename Storage<S>::T *ro
 #pragma unroll
             for (int j = 0; j < V - 1; ++j) v.e[j] = e[j + 1];
             v.e[V - 1] = from_right;
+            // a lane holding the row's end writes x = xb .. nx - 2 (x = nx - 1
+            // gets node 0's value); the warp's last lane leaves its last
+            // element to the next warp's first lane
             const bool has_row_end = xb + V > nx - 1;
             const bool last_foreign = (sub == W - 1) && (xb + V < nx);
-            if (!has_row_end && !last_foreign) {
-                st_vec<S>(rowp + xb, v);
-            } else {
-#pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    const int x = xb + j;
-                    const bool foreign = (x == nx - 1) || (j == V - 1 && last_foreign) || (x >= nx);
-                    if (!foreign) rowp[x] = v.e[j];
-                }
-            }
+            if (!has_row_end && !last_foreign) st_vec<S>(rowp + xb, v);
+            else st_head<S>(rowp + xb, v, has_row_end ? nx - 1 - xb : V - 1);
             if (xb == 0) rowp[nx - 1] = e[0];
             else if (sub == 0) rowp[xb - 1] = e[0];
         }

@@ -131,12 +131,10 @@ def push_pass(rows, v0, nx, ny, v, cx, cy, values):
             vec = np.concatenate([[from_left], e[:-1]])
             if not (sub == 0 or xb == 0):
                 row.write(xb, vec)
-            else:
-                for j in range(1, v):
-                    row.write(xb + j, vec[j])
-            for j in range(v):
-                if xb + j == nx - 1:
-                    row.write(0, e[j])
+            else:                                   # elements 1 .. v-1 only
+                row.write(xb + 1, vec[1:])
+            if xb + v > nx - 1:                     # node nx - 1 wraps to x = 0
+                row.write(0, e[nx - 1 - xb])
             if sub == WARP - 1 and xb + v < nx:
                 row.write(xb + v, e[v - 1])
         else:
@@ -146,12 +144,10 @@ def push_pass(rows, v0, nx, ny, v, cx, cy, values):
             last_foreign = sub == WARP - 1 and xb + v < nx
             if not has_row_end and not last_foreign:
                 row.write(xb, vec)
-            else:
-                for j in range(v):
-                    x = xb + j
-                    foreign = x == nx - 1 or (j == v - 1 and last_foreign) or x >= nx
-                    if not foreign:
-                        row.write(x, vec[j])
+            else:                                   # the first L elements only
+                n = nx - 1 - xb if has_row_end else v - 1
+                if n:
+                    row.write(xb, vec[:n])
             if xb == 0:
                 row.write(nx - 1, e[0])
             elif sub == 0:
