@@ -176,7 +176,7 @@ def test_fp64_collision_option_validation():
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
 def test_block_size_does_not_change_results(storage, layout):
-    """OLB_OPT_WARPS_PER_BLOCK only changes how row segments map to blocks
+    """OLB_OPT_WARPS_PER_BLOCK only changes how warp passes map to blocks
     (and, for the half formats, whether the register-capped A-B kernel runs):
     results are bitwise the same for 1, 2, 4 and 8 warps per block."""
     from paper_2501_16000_gb300 import binding as B
@@ -261,7 +261,7 @@ def test_half_precision_storage_short_runs(storage, bound, layout):
 @pytest.mark.parametrize("nx,ny", SIZES)
 def test_half_precision_ragged_sizes(nx, ny, layout, storage, bound):
     """The half formats on every ragged size (single nodes, single rows and
-    columns, partial vectors and segments) against the oracle, within the same
+    columns, partial vectors, warp passes spanning rows) against the oracle, within the same
     few-ulp bounds as the short-run test above, at even and odd times."""
     from paper_2501_16000_gb300.engine import Lattice
     f0 = random_state(nx, ny, "guided", 1.0 / 3.0, seed=nx * 7 + ny)
