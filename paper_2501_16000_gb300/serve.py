@@ -105,6 +105,12 @@ class Server:
     def close(self):
         self.engine.close()
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def request_bytes(self, case) -> int:
         """Device memory a request holds while admitted: its populations and,
         when fields are kept, the FP64 rho, u_x, u_y it is read back into."""
