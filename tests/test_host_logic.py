@@ -279,6 +279,13 @@ def test_autotune_picks_the_fastest_candidate_and_honours_the_cache(tmp_path):
     assert r2 == r and len(calls) == n                      # answered from the cache
     r3 = BT.autotune(BT_cases := W.batch_mix(16, seed=1), "f16", cache_path=path, measure=measure)
     assert len(calls) > n and BT.size_class(BT_cases) != BT.size_class(cases)
+    # the same lattices over more kernel classes (slots) are tuned anew
+    mix, classes = W.batch_mix(16, seed=1), W.batch_mix_classes(16, seed=1)
+    assert BT.kernel_classes(mix) == 1 and BT.kernel_classes(classes) == 6
+    assert [(c.nx, c.ny, c.tau) for c in mix] == [(c.nx, c.ny, c.tau) for c in classes]
+    n3 = len(calls)
+    BT.autotune(classes, "f16", cache_path=path, measure=measure)
+    assert len(calls) > n3
 
 
 def test_precision_router_rule():
