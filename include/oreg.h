@@ -45,7 +45,8 @@ typedef enum {
     OLB_ERR_NOMEM = 2,     /* device or host allocation failed */
     OLB_ERR_CUDA = 3,      /* a CUDA runtime call or launch failed */
     OLB_ERR_NONFINITE = 4, /* the state holds NaN or Inf (outputs still written) */
-    OLB_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    OLB_ERR_TIMEOUT = 5,   /* a bounded wait ended before the work it waits
+                              for (olb_batch_wait_for); that work goes on */
     OLB_ERR_STATE = 6      /* call not valid in the lattice's current state */
 } olb_status;
 
@@ -357,6 +358,13 @@ olb_status olb_batch_run(olb_batch *b, int64_t nrounds);
 
 /* Waits until the batch's enqueued rounds have finished. */
 olb_status olb_batch_wait(olb_batch *b);
+
+/* Waits at most `seconds` (>= 0) for the rounds enqueued so far: OLB_OK once
+ * they have finished, OLB_ERR_TIMEOUT if they are still running when the time
+ * is up (nothing is cancelled; a later wait can succeed), OLB_ERR_CUDA if the
+ * stream reported an error.  Polls an event recorded on the batch's stream,
+ * sleeping ~50 us between polls; seconds = 0 polls once. */
+olb_status olb_batch_wait_for(olb_batch *b, double seconds);
 
 /* Steps a member still has to take. */
 olb_status olb_batch_remaining(const olb_batch *b, const olb_lattice *lat, int64_t *steps);

@@ -114,8 +114,18 @@ class BatchEngine:
         stream.wait_event(after)
         return lat.read_back_on(stream, keep_fields)
 
-    def wait(self) -> None:
-        B.call("olb_batch_wait", self._h)
+    def wait(self, timeout: float | None = None) -> bool:
+        """Waits for the enqueued rounds: without a timeout until they have
+        finished; with one at most `timeout` seconds, returning False if they
+        are still running then (nothing is cancelled)."""
+        if timeout is None:
+            B.call("olb_batch_wait", self._h)
+            return True
+        st = B.load().olb_batch_wait_for(self._h, float(timeout))
+        if st == B.OLB_ERR_TIMEOUT:
+            return False
+        B.check(st, "olb_batch_wait_for")
+        return True
 
     def close(self) -> None:
         if self._h is not None:

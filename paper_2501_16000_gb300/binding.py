@@ -101,6 +101,7 @@ SIGNATURES = {
     "olb_batch_remove": (ctypes.c_int, [_h, _h]),
     "olb_batch_run": (ctypes.c_int, [_h, ctypes.c_int64]),
     "olb_batch_wait": (ctypes.c_int, [_h]),
+    "olb_batch_wait_for": (ctypes.c_int, [_h, ctypes.c_double]),
     "olb_batch_remaining": (ctypes.c_int, [_h, _h, _P(ctypes.c_int64)]),
     "olb_batch_size": (ctypes.c_int32, [_h]),
     "olb_batch_work_items": (ctypes.c_int64, [_h]),

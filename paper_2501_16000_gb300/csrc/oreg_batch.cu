@@ -4,11 +4,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "oreg.h"
@@ -152,6 +155,7 @@ struct olb_batch {
     cudaStream_t side[SIDE_STREAMS];
     cudaEvent_t fork_ev, join_ev[SIDE_STREAMS];
     int nside;              // side streams created so far
+    cudaEvent_t wait_ev;    // olb_batch_wait_for (created on first use)
 };
 
 namespace {
@@ -499,6 +503,24 @@ olb_status olb_batch_wait(olb_batch *b) {
     return OLB_OK;
 }
 
+olb_status olb_batch_wait_for(olb_batch *b, double seconds) {
+    if (!b) return bfail(OLB_ERR_INVALID, "batch is NULL");
+    if (!(seconds >= 0) || !std::isfinite(seconds))
+        return bfail(OLB_ERR_INVALID, "seconds must be finite and >= 0 (got %g)", seconds);
+    if (!b->wait_ev)
+        B_CUDA(cudaEventCreateWithFlags(&b->wait_ev, cudaEventDisableTiming), "creating the wait event");
+    B_CUDA(cudaEventRecord(b->wait_ev, b->stream), "recording the wait event");
+    const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(seconds);
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(b->wait_ev);
+        if (e == cudaSuccess) return OLB_OK;
+        if (e != cudaErrorNotReady) return bcuda(e, "waiting for the batch");
+        if (std::chrono::steady_clock::now() >= until)
+            return bfail(OLB_ERR_TIMEOUT, "batch rounds still running after %g s", seconds);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
 olb_status olb_batch_remaining(const olb_batch *b, const olb_lattice *lat, int64_t *steps) {
     if (!b || !lat || !steps) return bfail(OLB_ERR_INVALID, "NULL argument");
     for (const Member &m : b->members)
@@ -535,6 +557,7 @@ olb_status olb_batch_destroy(olb_batch *b) {
         cudaEventDestroy(b->join_ev[i]);
     }
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->wait_ev) cudaEventDestroy(b->wait_ev);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return st;

@@ -85,10 +85,13 @@ def _bytes(lat_case, storage, layout):
 class Server:
     def __init__(self, storage="f16", layout="ab", budget_bytes=120e9, steps_per_launch=100,
                  max_lattices=8192, max_items=1 << 24, warps_per_block=4, blocks_per_sm=0,
-                 keep_fields=True, engine=None, item_passes=ITEM_PASSES):
+                 keep_fields=True, engine=None, item_passes=ITEM_PASSES, round_timeout_s=None):
         """``engine`` replaces the BatchEngine (anything with its new_lattice,
         add, remove, remaining, run, record_event, read_back and close
-        methods)."""
+        methods).  ``round_timeout_s``: if set, the host waits at most this
+        long for each enqueued round (polling its event) and ``run`` raises
+        TimeoutError when a round has not finished by then, instead of
+        blocking on a stalled device."""
         self.storage, self.layout = storage, layout
         self.budget = float(budget_bytes)
         self.keep_fields = keep_fields
@@ -98,6 +101,7 @@ class Server:
             blocks_per_sm=blocks_per_sm, item_passes=item_passes)
         self.item_passes = int(item_passes)
         self.max_items = max_items
+        self.round_timeout_s = round_timeout_s
         self.rounds = 0
         self.peak_bytes = 0
         self.peak_inflight = 0
@@ -110,6 +114,16 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+    def _wait_round(self, ev) -> None:
+        if self.round_timeout_s is None:
+            ev.synchronize()
+            return
+        until = time.perf_counter() + self.round_timeout_s
+        while not ev.query():
+            if time.perf_counter() >= until:
+                raise TimeoutError(f"a batch round did not finish within {self.round_timeout_s} s")
+            time.sleep(5e-5)
 
     def request_bytes(self, case) -> int:
         """Device memory a request holds while admitted: its populations and,
@@ -212,10 +226,10 @@ class Server:
                     # round r + 1 is enqueued before the host waits for round r
                     rounds.append(ev)
                     if len(rounds) > 1:
-                        rounds.popleft().synchronize()
+                        self._wait_round(rounds.popleft())
                     continue
                 while rounds:
-                    rounds.popleft().synchronize()
+                    self._wait_round(rounds.popleft())
                 # idle: wait for the next arrival or a read-back
                 wait = 0.01
                 if pending:

@@ -96,6 +96,29 @@ def test_many_slots_overlap_and_stay_bitwise(layout):
             assert np.array_equal(ref.populations(), g), c
 
 
+def test_bounded_wait_reports_running_rounds():
+    """olb_batch_wait_for returns OLB_ERR_TIMEOUT (False here) while enqueued
+    rounds are still running, without cancelling them; a later wait finishes
+    and the lattice has advanced every enqueued step, as without the timeout."""
+    from paper_2501_16000_gb300.batch import BatchEngine
+    from paper_2501_16000_gb300.engine import Lattice
+    case = W.LatticeCase(nx=4096, ny=4096, tau=0.8, case="shear", u0=0.05, m=1, n=1)
+    with BatchEngine("f32", "ab", max_lattices=2, max_items=1 << 16, steps_per_launch=50) as eng:
+        lat = eng.new_lattice(case)
+        eng.add(lat, 1000)
+        eng.run(20)                      # 1000 steps of 16.8 M nodes, ~0.2 s of work
+        assert eng.wait(timeout=0.0) is False
+        assert eng.wait(timeout=60.0) is True
+        assert lat.time == 1000 and eng.remaining(lat) == 0
+        got = lat.diagnostics()
+        lat.close()
+    with Lattice(case.nx, case.ny, case.tau, storage="f32", layout="ab") as ref:
+        ref.init_case(case)
+        ref.step(1000)
+        want = ref.diagnostics()
+    assert got == want
+
+
 def test_batch_fp64_matches_oracle():
     from paper_2501_16000_gb300.batch import BatchEngine
     cases = mixed_cases()[:6]

@@ -142,6 +142,37 @@ class _Done:
     def synchronize(self):
         pass
 
+    def query(self):
+        return True
+
+
+class _Stalled:
+    """An event of a round that never finishes (a stalled device)."""
+
+    def synchronize(self):
+        raise AssertionError("an unbounded wait on a stalled round")
+
+    def query(self):
+        return False
+
+
+def test_server_reports_a_stalled_round_within_its_timeout():
+    """With round_timeout_s the server polls each round's event and raises
+    TimeoutError once the limit has passed, instead of blocking on a round
+    that never finishes (a fake event stands in for a stalled GPU)."""
+    from paper_2501_16000_gb300 import build
+    build.build()                                   # request_bytes is a host-only library call
+    from paper_2501_16000_gb300.serve import Server
+    eng = _FakeEngine(K=10)
+    eng.record_event = lambda: _Stalled()
+    trace = [W.Request(0, 0.0, W.LatticeCase(nx=8, ny=8, tau=0.8, steps=100))]
+    srv = Server(engine=eng, budget_bytes=1e9, round_timeout_s=0.05)
+    t0 = time.perf_counter()
+    with pytest.raises(TimeoutError):
+        srv.run(trace)
+    assert time.perf_counter() - t0 < 5.0
+    assert eng.rounds >= 2            # round r + 1 was enqueued before waiting for round r
+
 
 def test_serving_admission_fifo_and_budget():
     from paper_2501_16000_gb300 import build
