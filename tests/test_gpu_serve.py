@@ -45,6 +45,38 @@ def test_served_results_equal_alone(layout):
         assert by_id[req.rid].latency_s >= 0
 
 
+def test_served_requests_of_many_kernel_classes_equal_alone():
+    """Requests of six kernel / constant classes (OReg and BGK, guided at two
+    temperatures and polynomial) arriving while others run: new classes join
+    mid-run (the batch graph is captured again, each class on its own capture
+    stream), and every result is still bitwise that of the request alone."""
+    import dataclasses
+
+    from paper_2501_16000_gb300.engine import Lattice
+    from paper_2501_16000_gb300.serve import Server
+    trace = small_trace(n=12, seed=17)
+    classes = []
+    for j, req in enumerate(sorted(trace, key=lambda r: r.arrival_s)):
+        poly = (j // 2) % 2 == 1
+        lat = dataclasses.replace(req.lattice, coll="bgk" if j % 2 else "oreg",
+                                  eq="poly2" if poly else "guided",
+                                  theta=1.0 / 3.0 if poly else (0.30 if (j // 4) % 2 else 0.36))
+        classes.append(dataclasses.replace(req, lattice=lat))
+    srv = Server("f16", "ab", budget_bytes=1e9, steps_per_launch=16)
+    results, _ = srv.run(classes)
+    srv.close()
+    assert len(results) == len(classes) and srv.peak_inflight > 1
+    by_id = {r.rid: r for r in results}
+    for req in classes:
+        c = req.lattice
+        with Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, "f16", "ab") as lat:
+            lat.init_case(c)
+            lat.step(c.steps)
+            alone = lat.moments()
+        for a, b in zip(alone, by_id[req.rid].fields):
+            assert np.array_equal(a, b), (req.rid, c.coll, c.eq, c.theta)
+
+
 def test_admission_respects_the_budget():
     from paper_2501_16000_gb300.serve import Server
     trace = small_trace(n=10, seed=3)
