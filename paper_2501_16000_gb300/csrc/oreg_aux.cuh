@@ -221,9 +221,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Storage<S
 #pragma unroll
     for (int i = 0; i < 9; ++i) sum_shift += (C)kd.shift[dcls(i)];
     const long long N = (long long)g.nx * g.ny;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / g.nx), x = (int)(n % g.nx);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // (x, y) of node n, advanced by the grid stride without a division per node
+    int yn = (int)(n / g.nx), xn = (int)(n % g.nx);
+    const int sy = (int)(stride / g.nx), sx = (int)(stride % g.nx);
+    for (; n < N; n += stride) {
+        const int y = yn, x = xn;
+        xn += sx;
+        yn += sy;
+        if (xn >= g.nx) {
+            xn -= g.nx;
+            ++yn;
+        }
         C v[9];
         bool finite = true;
 #pragma unroll
