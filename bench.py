@@ -13,7 +13,8 @@ oracle on the host cores instead (bounded sample of the same workload).
 
 Multi-GPU (torchrun, one rank per GPU): every rank advances its own
 independent lattice (weak scaling, no data-path collective); the timing is
-the max over ranks.
+the max over ranks.  The CPU baseline and the extended sections (precision,
+batched, serving, Mach sweep) run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -391,14 +392,16 @@ def run_native(args):
             e2e_500 = solve(500)
     lat.close()
     extra = {}
-    if rank == 0 and not args.no_extended:
+    # the extended sections and the CPU baseline are single-GPU measurements:
+    # at N > 1 they are left out, so that the other GPUs are not held meanwhile
+    if rank == 0 and world == 1 and not args.no_extended:
         extra["precision_vs_fp64"] = precision_section(args)
         extra["batched"] = batched_section(args)
         extra["serving"] = serving_section(args, extra["batched"])
         extra["mach_sweep"] = mach_sweep_section()
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, case, args.cpu_seconds)
 
     if rank == 0:
