@@ -376,17 +376,24 @@ def run_native(args):
         def solve(k):
             barrier()
             t0 = time.perf_counter()
-            lat.init_fields(h[0].numpy(), h[1].numpy(), h[2].numpy())
+            lat.init_fields(h[0].numpy(), h[1].numpy(), h[2].numpy())   # waits for its copies
+            t1 = time.perf_counter()
             lat.step(k)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
             B.call("olb_moments", lat.handle, *outs, None)
             barrier()
-            secs = max_over_ranks(time.perf_counter() - t0, "cuda")
+            t3 = time.perf_counter()
+            secs = max_over_ranks(t3 - t0, "cuda")
             return {"value": round(world * N * k / secs / 1e6, 1), "unit": "MLUPS",
                     "h2d_bytes_per_step": int(3 * N * 8 / k),
                     "d2h_bytes_per_step": int(3 * N * 8 / k), "steps": k,
                     "note": f"one solve of {k} steps: olb_init_fields from pinned host "
                             f"fields ({3 * N * 8 / 1e9:.2f} GB), olb_step, olb_moments to "
-                            f"pinned host arrays ({3 * N * 8 / 1e9:.2f} GB)"}
+                            f"pinned host arrays ({3 * N * 8 / 1e9:.2f} GB)",
+                    "phases_ms": {"init_fields": round((t1 - t0) * 1e3, 1),
+                                  "steps": round((t2 - t1) * 1e3, 1),
+                                  "moments": round((t3 - t2) * 1e3, 1)}}
         e2e = solve(K)
         if K != 500:
             e2e_500 = solve(500)
