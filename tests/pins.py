@@ -410,7 +410,8 @@ def _decay_ratio(nx, ny, m, n, tau, theta, coll, steps, u0=0.05, eq=O.GUIDED):
             f = O.run(f, p, every)
     ts, amps = np.array(ts), np.array(amps)
     sel = ts >= max(20, 20 * tau)
-    gamma = -np.polyfit(ts[sel], np.log(amps[sel]), 1)[0]
+    with np.errstate(invalid="ignore", divide="ignore"):   # a planted mistake may flip the sign
+        gamma = -np.polyfit(ts[sel], np.log(amps[sel]), 1)[0]
     return gamma / W.wave_number_sq(nx, ny, m, n) / (theta * (tau - 0.5))
 
 
