@@ -359,7 +359,7 @@ olb_status olb_batch_run(olb_batch *b, int64_t nrounds);
 /* Waits until the batch's enqueued rounds have finished. */
 olb_status olb_batch_wait(olb_batch *b);
 
-/* Waits at most `seconds` (>= 0) for the rounds enqueued so far: OLB_OK once
+/* Waits at most `seconds` (0 .. 1e6) for the rounds enqueued so far: OLB_OK once
  * they have finished, OLB_ERR_TIMEOUT if they are still running when the time
  * is up (nothing is cancelled; a later wait can succeed), OLB_ERR_CUDA if the
  * stream reported an error.  Polls an event recorded on the batch's stream,
