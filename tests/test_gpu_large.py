@@ -110,3 +110,37 @@ def test_compare_finds_a_planted_difference():
         lat.set_populations(fl, lat.time)
         d, _ = lat.compare(ref)
         assert math.isinf(d)
+
+
+def test_512_lattice_mix_in_the_benchmarked_batch_configuration():
+    """The benchmark's batched workload (all 512 lattices of the mix, FP16)
+    in the configuration the tuner picks for it on this machine (A-B, an
+    oversubscribed grid, 4 warp passes per item, 200 steps per replay): a
+    sample of the lattices, small and large, shear and shock, ends bitwise
+    equal to the same lattice advanced alone."""
+    from paper_2501_16000_gb300.batch import BatchEngine, work_items
+    from paper_2501_16000_gb300.engine import Lattice
+    steps = 230                                  # one full replay and part of a second
+    cases = W.batch_mix(512, seed=1, steps=steps)
+    R, K = 4, 200
+    items = sum(work_items(c.nx, c.ny, "f16", R) for c in cases)
+    by_size = sorted(range(len(cases)), key=lambda j: cases[j].nodes)
+    sample = sorted(set(by_size[:3] + by_size[-3:] + by_size[250:252] +
+                        [j for j in range(len(cases)) if cases[j].case == "shock"][:2]))
+    with BatchEngine("f16", "ab", max_lattices=len(cases), max_items=items, steps_per_launch=K,
+                     warps_per_block=2, blocks_per_sm=128, item_passes=R) as eng:
+        lats = [eng.new_lattice(c) for c in cases]
+        for lat in lats:
+            eng.add(lat, steps)
+        eng.run(2)
+        eng.wait()
+        got = {j: lats[j].populations() for j in sample}
+        assert all(lat.time == steps for lat in lats)
+        for lat in lats:
+            lat.close()
+    for j in sample:
+        c = cases[j]
+        with Lattice(c.nx, c.ny, c.tau, c.theta, c.eq, c.coll, "f16", "ab") as ref:
+            ref.init_case(c)
+            ref.step(steps)
+            assert np.array_equal(ref.populations(), got[j]), (j, c.nx, c.ny, c.case)
