@@ -26,7 +26,7 @@ __host__ __device__ constexpr bool aa_odd_capped() {
 
 // ---------------------------------------------------------------------------
 // Stream-collide, A-B layout.  A buffer holds post-collision populations at
-// the node that produced them.  A warp gathers, for 32*V nodes of one row,
+// the node that produced them.  A warp gathers, for the 32*V nodes of a pass,
 // f_i(x) = post_i(x - c_i) from src (the streaming of Eqs. 1/7 as a pull),
 // which is the pre-collision state S_t(x); it collides and stores post(x) to
 // dst at x.
@@ -43,8 +43,8 @@ __device__ __forceinline__ RawRow<S> fetch_plane(const typename Storage<S>::T *b
     return fetch_row<S, cx_of(I), !AA_ODD>(base + P * plane + (size_t)ys * pitch, xb, nx, sub, W);
 }
 
-// Gathers the pre-collision populations of the warp's 32*V nodes: all nine
-// row fetches are issued before any is decoded.
+// Gathers the pre-collision populations of the warp pass's 32*V nodes: all
+// nine row fetches are issued before any is decoded.
 template <int S, bool AA_ODD>
 __device__ __forceinline__ void pull_all(const typename Storage<S>::T *base, size_t plane,
                                          int pitch, int y, int ny, int xb, int nx, int sub, int W,
