@@ -69,8 +69,8 @@ __device__ __forceinline__ void pull_all(const typename Storage<S>::T *base, siz
     shift_row<S, cx_of(8)>(r8, xb, nx, sub, W, f[8]);
 }
 
-// Row padding (positions nx .. pitch-1 of the last vector of a row) is kept
-// at g = 0 so that it never holds values that are not finite.
+// Row padding (positions nx .. pitch-1 of the last vector of a row) gets g = 0
+// (the AA push may also copy finite node values there): never a non-finite.
 template <int S>
 __device__ __forceinline__ void zero_padding(typename Storage<S>::C f[9][Storage<S>::V], int xb,
                                              int nx) {
